@@ -1,0 +1,598 @@
+"""Plain FP64 CPU oracle of PDLP (restarted PDHG for LP).
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import this module:
+only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline legs of
+``bench.py`` use it.  It shares no code with the CUDA path.
+
+It restates the method of "PDLP: A Practical First-Order Method for Large-Scale
+Linear Programming" step by step, in the paper's order and notation, with numpy
+vector operations and scipy's CSR matrix-vector product as the only library
+primitives.  Everything is float64, evaluated in plain index order.
+
+Problem (Sec. 2, Eq. (1)):   min c'x  s.t.  lc <= Ax <= uc,  lv <= x <= uv.
+Saddle form (Eq. (2)):       L(x,y) = c'x - y'Ax - p(y; -uc, -lc)  over X x Y.
+
+Readings taken where the paper is silent or ambiguous (each is repeated where it is
+used):
+  R1  z^{0,0}: x = proj_X(0), y = 0.
+  R2  ||A||_inf in eta_hat^{0,0} = 1/||A||_inf is the largest absolute entry of the
+      preconditioned matrix (1 if the matrix has no nonzero).
+  R3  k in Algorithm 2 counts accepted iterations only, and the step-size factors use
+      (k+2) with that 0-based k: with (k+1) the very first step would give
+      (1 - 1^-0.3) = 0 and eta_hat would stay 0 forever.
+  R4  Restart/termination are evaluated when the total count k is a multiple of 64;
+      condition (iii) is tested after every accepted iteration.
+  R5  (i)/(ii) need mu(z^{n,0}, z^{n-1,0}); they are off until the first restart.
+  R6  mu_c of the "previous" candidate in (ii) is the candidate mu from the previous
+      evaluation in the same outer loop (+inf if none).
+  R7  mu(z^{n,0}, z^{n-1,0}) is evaluated once, right after the restart, with the
+      updated primal weight.
+  R8  A tie mu(current) == mu(average) picks the average ("otherwise").
+  R9  Termination is tested on the restart candidate at each 64-check (and on z^{0,0}
+      before the first step); the returned point is that candidate.
+  R10 Relative KKT error on the unscaled LP (see ``kkt_stats``).
+  R11 0 * inf = 0 in the dual objective (the sign sets make the multiplier 0).
+  R12 Relative gap 0/0 = 0.
+  R13 A zero row/column gets scaling factor 1.
+  R14 Ruiz row and column factors are both computed from the same current matrix.
+  R16 The retry loop of Algorithm 2 is capped (``max_step_retries``).
+  R17 The dual step is evaluated as  y' = yhat - proj_[-sigma uc, -sigma lc](yhat)
+      with yhat = y - sigma (2 A x' - A x): the same map as Eq. (3b) (Appendix B's
+      Moreau form with sigma pulled into the interval), written so that the case
+      analysis of Sec. 2 holds exactly in floating point (y' in Y bit for bit).
+  R18 A x of the running average is obtained from the running sum of A x^{n,i}
+      (linearity), A'y likewise.
+  R19 The interaction term of Eq. (5) / Algorithm 2 is taken in magnitude,
+      2|(y'-y)'A(x'-x)|.  Eq. (5) is Chambolle-Pock's condition written for their
+      operator K = -A (App. B); under the dual step (3b), which moves y along
+      -A(2x'-x), the signed term (y'-y)'A(x'-x) is negative on typical steps, and the
+      literal formula then never limits eta (eta grows without bound and the
+      iteration diverges).  With the magnitude, eta_bar >= 1/||A||_2 still holds.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+import scipy.sparse as sp
+
+# status codes (same meaning as the C-ABI's)
+OPTIMAL = 0
+ITERATION_LIMIT = 1
+TIME_LIMIT = 2
+PRIMAL_INFEASIBLE = 3
+DUAL_INFEASIBLE = 4
+NUMERICAL_ERROR = 5
+
+RESTART_NONE, RESTART_SUFFICIENT, RESTART_NECESSARY, RESTART_ARTIFICIAL = 0, 1, 2, 3
+
+
+@dataclasses.dataclass
+class Params:
+    """Algorithm constants; defaults are the paper's (Sec. 3 and Sec. 7)."""
+
+    eps_rel_kkt: float = 1e-8
+    termination_mode: int = 0  # 0: relative KKT (R10); 1: paper's l_inf + relative gap, Eq. (9)
+    eps_abs_feas: float = 1e-8
+    eps_rel_gap: float = 1e-2
+    max_iters: int = 1_000_000
+    ruiz_iters: int = 10
+    pc_alpha: float = 1.0
+    check_period: int = 64
+    beta_suff: float = 0.1
+    beta_nec: float = 0.9
+    beta_art: float = 0.5
+    theta: float = 0.5
+    eps_zero: float = 1e-10
+    max_step_retries: int = 60
+    # oracle-only switches used by pin tests (no counterpart in the CUDA path)
+    fixed_step: float | None = None  # constant eta, no adaptive step (Chambolle-Pock)
+    fixed_omega: float | None = None
+    restarts: bool = True
+
+
+# ----------------------------------------------------------------------------
+# small helpers, each a definition from Sec. 2
+# ----------------------------------------------------------------------------
+
+def proj_box(v, lo, hi):
+    """Orthogonal projection onto the box [lo, hi] (Sec. 2, "Notation")."""
+    return np.minimum(np.maximum(v, lo), hi)
+
+
+def pos(v):
+    """v^+ = max(0, v) (Sec. 2, "Notation")."""
+    return np.maximum(v, 0.0)
+
+
+def neg(v):
+    """v^- = -min(0, v) (Sec. 2, "Notation")."""
+    return -np.minimum(v, 0.0)
+
+
+def p_fn(y, lo, hi):
+    """p(y; l, u) = u'y^+ - l'y^- (Sec. 2), with 0*inf = 0 (R11)."""
+    yp, yn = pos(y), neg(y)
+    with np.errstate(invalid="ignore"):
+        t1 = np.where(yp > 0, hi * yp, 0.0)
+        t2 = np.where(yn > 0, lo * yn, 0.0)
+    return float(np.sum(t1) - np.sum(t2))
+
+
+def combine(lc, uc):
+    """Combine(lc, uc)_i = max{0, |lc_i|*, |uc_i|*} with |v|* = |v| if finite else 0
+    (Sec. 3, "Initialization of the primal weights")."""
+    lf = np.where(np.isfinite(lc), np.abs(lc), 0.0)
+    uf = np.where(np.isfinite(uc), np.abs(uc), 0.0)
+    return np.maximum(0.0, np.maximum(lf, uf))
+
+
+def norm2(v):
+    return math.sqrt(float(np.dot(v, v)))
+
+
+def proj_R(g, lv, uv):
+    """Projection onto the reduced-cost sign set R (Sec. 2, Eq. (1)): {0} for a free
+    variable, R^- for only an upper bound, R^+ for only a lower bound, R otherwise."""
+    lf, uf = np.isfinite(lv), np.isfinite(uv)
+    r = g.copy()
+    r = np.where(lf & ~uf, np.maximum(g, 0.0), r)
+    r = np.where(~lf & uf, np.minimum(g, 0.0), r)
+    r = np.where(~lf & ~uf, 0.0, r)
+    return r
+
+
+# ----------------------------------------------------------------------------
+# diagonal preconditioning (Sec. 3, "Diagonal Preconditioning")
+# ----------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class ScaledLP:
+    """The preconditioned instance: A~ = D1 A D2, c~ = D2 c, (lc~, uc~) = D1 (lc, uc),
+    (lv~, uv~) = D2^-1 (lv, uv); x = D2 x~ and y = D1 y~ map back."""
+
+    A: sp.csr_matrix
+    AT: sp.csr_matrix
+    c: np.ndarray
+    lc: np.ndarray
+    uc: np.ndarray
+    lv: np.ndarray
+    uv: np.ndarray
+    d1: np.ndarray
+    d2: np.ndarray
+    orig: object  # the unscaled instance (lpgen.LPInstance-like)
+    A_orig: sp.csr_matrix
+
+
+def _row_max_abs(M):
+    """||M_j,.||_inf for every row (0 for an empty row)."""
+    M = M.tocsr()
+    out = np.zeros(M.shape[0])
+    nz = np.diff(M.indptr) > 0
+    if M.nnz:
+        out[nz] = np.maximum.reduceat(np.abs(M.data), M.indptr[:-1][nz])
+    return out
+
+
+def _row_pnorm(M, p):
+    """||M_j,.||_p for every row (0 for an empty row)."""
+    M = M.tocsr()
+    out = np.zeros(M.shape[0])
+    nz = np.diff(M.indptr) > 0
+    if M.nnz:
+        a = np.abs(M.data)
+        if p == 1.0:
+            out[nz] = np.add.reduceat(a, M.indptr[:-1][nz])
+        else:
+            out[nz] = np.add.reduceat(a ** p, M.indptr[:-1][nz]) ** (1.0 / p)
+    return out
+
+
+def _apply_factors(M, fr, fs):
+    """A~_ij <- (A~_ij * fr_i) * fs_j, the same rounding order for every entry."""
+    M = M.tocsr(copy=True)
+    rows = np.repeat(np.arange(M.shape[0]), np.diff(M.indptr))
+    M.data = (M.data * fr[rows]) * fs[M.indices]
+    return M
+
+
+def precondition(inst, ruiz_iters=10, pc_alpha=1.0) -> ScaledLP:
+    """``ruiz_iters`` Ruiz passes, then one Pock-Chambolle pass with ``pc_alpha``.
+
+    Ruiz (Sec. 3): (D1)_jj = 1/sqrt(||A_j,.||_inf), (D2)_ii = 1/sqrt(||A_.,i||_inf),
+    both from the current matrix (R14), applied repeatedly.  Pock-Chambolle:
+    (D1)_jj = 1/sqrt(||A_j,.||_{2-alpha}), (D2)_ii = 1/sqrt(||A_.,i||_alpha).
+    A zero row/column keeps factor 1 (R13)."""
+    A = sp.csr_matrix((inst.val.astype(np.float64), inst.col_idx, inst.row_ptr),
+                      shape=(inst.m, inst.n))
+    m, n = A.shape
+    d1 = np.ones(m)
+    d2 = np.ones(n)
+    At = A.copy()
+    for _ in range(ruiz_iters):
+        r = _row_max_abs(At)
+        s = _row_max_abs(At.T.tocsr())
+        with np.errstate(divide="ignore"):
+            fr = np.where(r > 0, 1.0 / np.sqrt(r), 1.0)
+            fs = np.where(s > 0, 1.0 / np.sqrt(s), 1.0)
+        At = _apply_factors(At, fr, fs)
+        d1 = d1 * fr
+        d2 = d2 * fs
+    if pc_alpha is not None and pc_alpha > 0:
+        r = _row_pnorm(At, 2.0 - pc_alpha)
+        s = _row_pnorm(At.T.tocsr(), pc_alpha)
+        with np.errstate(divide="ignore"):
+            fr = np.where(r > 0, 1.0 / np.sqrt(r), 1.0)
+            fs = np.where(s > 0, 1.0 / np.sqrt(s), 1.0)
+        At = _apply_factors(At, fr, fs)
+        d1 = d1 * fr
+        d2 = d2 * fs
+    return ScaledLP(
+        A=At,
+        AT=At.T.tocsr(),
+        c=d2 * inst.c,
+        lc=d1 * inst.lc,
+        uc=d1 * inst.uc,
+        lv=inst.lv / d2,
+        uv=inst.uv / d2,
+        d1=d1,
+        d2=d2,
+        orig=inst,
+        A_orig=A,
+    )
+
+
+def initial_primal_weight(c, lc, uc):
+    """InitializePrimalWeight (Sec. 3): ||c||_2 / ||Combine(lc,uc)||_2 if both are
+    positive, else 1."""
+    nc = norm2(c)
+    nb = norm2(combine(lc, uc))
+    if nc > 0.0 and nb > 0.0:
+        return nc / nb
+    return 1.0
+
+
+def primal_weight_update(x_new, y_new, x_old, y_old, omega, theta=0.5, eps_zero=1e-10):
+    """Algorithm 3: log-space smoothing of Delta_y / Delta_x when both distances lie in
+    (eps_zero, 1/eps_zero); otherwise the weight is kept."""
+    dx = norm2(x_new - x_old)
+    dy = norm2(y_new - y_old)
+    if eps_zero < dx < 1.0 / eps_zero and eps_zero < dy < 1.0 / eps_zero:
+        return math.exp(theta * math.log(dy / dx) + (1.0 - theta) * math.log(omega))
+    return omega
+
+
+# ----------------------------------------------------------------------------
+# the PDHG step (Eq. (3), Algorithm 2)
+# ----------------------------------------------------------------------------
+
+def primal_step(x, ATy, c, lv, uv, tau):
+    """Eq. (3a): x' = proj_X(x - tau (c - A'y))."""
+    return proj_box(x - tau * (c - ATy), lv, uv)
+
+
+def dual_step(y, Ax, Ax_new, lc, uc, sigma):
+    """Eq. (3b): y' = y - sigma A(2x'-x) - sigma proj_[-uc,-lc](y/sigma - A(2x'-x)),
+    evaluated as yhat - proj_[-sigma uc, -sigma lc](yhat) with
+    yhat = y - sigma (2 A x' - A x) (R17, R18)."""
+    yhat = y - sigma * (2.0 * Ax_new - Ax)
+    return yhat - proj_box(yhat, -sigma * uc, -sigma * lc)
+
+
+def step_factors(k):
+    """The reduction and growth factors of Algorithm 2 at accepted count k (R3)."""
+    kk = float(k + 2)
+    return 1.0 - kk ** (-0.3), 1.0 + kk ** (-0.6)
+
+
+def adaptive_step(lp: ScaledLP, x, y, Ax, ATy, omega, eta_hat, k, max_retries):
+    """Algorithm 2 (AdaptiveStepOfPDHG).  Returns (x', y', Ax', eta, eta', attempts,
+    ok); ``ok`` is False when the retry cap (R16) is hit or the step is not finite."""
+    eta = eta_hat
+    red, grow = step_factors(k)
+    for attempt in range(1, max_retries + 1):
+        xn = primal_step(x, ATy, lp.c, lp.lv, lp.uv, eta / omega)
+        Axn = lp.A @ xn
+        yn = dual_step(y, Ax, Axn, lp.lc, lp.uc, eta * omega)
+        dx = xn - x
+        dy = yn - y
+        num = omega * float(np.dot(dx, dx)) + float(np.dot(dy, dy)) / omega
+        den = 2.0 * abs(float(np.dot(dy, Axn - Ax)))  # R19
+        eta_bar = num / den if den > 0.0 else math.inf
+        eta_new = min(red * eta_bar, grow * eta)
+        if not (math.isfinite(eta_new) and math.isfinite(num)):
+            return xn, yn, Axn, eta, eta_new, attempt, False
+        if eta <= eta_bar:
+            return xn, yn, Axn, eta, eta_new, attempt, True
+        eta = eta_new
+    return xn, yn, Axn, eta, eta, max_retries, False
+
+
+# ----------------------------------------------------------------------------
+# normalized duality gap (Sec. 3, "Adaptive restarts")
+# ----------------------------------------------------------------------------
+
+def normalized_gap(lp: ScaledLP, x, y, Ax, ATy, x_ref, y_ref, omega):
+    """mu_n(z, z_ref) = rho_r(z) with r = ||z - z_ref||_omega, where
+    rho_r(z) = (1/r) max { L(x, yh) - L(xh, y) : zh in X x Y, ||zh - z||_omega <= r }.
+
+    L(x,yh) - L(xh,y) = -g'(xh - x) + sum_i [h_i(yh_i) - h_i(y_i)] with g = c - A'y and
+    h_i(s) = (lc_i - (Ax)_i) s for s > 0, (uc_i - (Ax)_i) s for s < 0 (the objective of
+    the max, written relative to its value 0 at zh = z).  For a multiplier on the
+    ball, parametrised by s = 1/lambda >= 0, the maximiser is coordinate-wise
+        xh = proj_[lv,uv](x - (s/omega) g),
+        yh = y + s omega a   if lc finite and that is > 0      (a = lc - Ax),
+             y + s omega b   elif uc finite and that is < 0    (b = uc - Ax),
+             0               otherwise,
+    and ||zh(s) - z||_omega is nondecreasing in s.  The radius is met by bisection
+    on s to relative width 1e-14; if every coordinate saturates at a finite
+    distance within the ball, the saturated point is the maximiser."""
+    dxr = x - x_ref
+    dyr = y - y_ref
+    r = math.sqrt(omega * float(np.dot(dxr, dxr)) + float(np.dot(dyr, dyr)) / omega)
+    if r == 0.0:
+        return 0.0
+    g = lp.c - ATy
+    lcf = np.isfinite(lp.lc)
+    ucf = np.isfinite(lp.uc)
+    with np.errstate(invalid="ignore"):
+        a = np.where(lcf, lp.lc - Ax, -np.inf)
+        b = np.where(ucf, lp.uc - Ax, np.inf)
+
+    def hfun(v):
+        with np.errstate(invalid="ignore"):
+            return np.where(v > 0, a * v, np.where(v < 0, b * v, 0.0))
+
+    hy = hfun(y)
+
+    def trial(s):
+        xh = proj_box(x - (s / omega) * g, lp.lv, lp.uv)
+        with np.errstate(invalid="ignore", over="ignore"):
+            sp_ = y + (s * omega) * np.where(lcf, a, 0.0)
+            sm_ = y + (s * omega) * np.where(ucf, b, 0.0)
+        yh = np.where(lcf & (sp_ > 0), sp_, np.where(ucf & (sm_ < 0), sm_, 0.0))
+        return xh, yh
+
+    def dist(s):
+        xh, yh = trial(s)
+        ex, ey = xh - x, yh - y
+        return math.sqrt(omega * float(np.dot(ex, ex)) + float(np.dot(ey, ey)) / omega)
+
+    def objective(s):
+        xh, yh = trial(s)
+        return float(-np.dot(g, xh - x) + np.sum(hfun(yh) - hy))
+
+    # Does every coordinate stop moving at a finite s?
+    x_unb = ((g > 0) & ~np.isfinite(lp.lv)) | ((g < 0) & ~np.isfinite(lp.uv))
+    y_unb = (lcf & (a > 0)) | (ucf & (b < 0))
+    if not (x_unb.any() or y_unb.any()):
+        bps = [0.0]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            gx = np.abs(g)
+            room = np.where(g > 0, x - lp.lv, np.where(g < 0, lp.uv - x, 0.0))
+            bx = np.where(gx > 0, omega * room / gx, 0.0)
+            by1 = np.where(lcf & (a < 0), -y / (omega * a), 0.0)
+            by2 = np.where(ucf & (b > 0), -y / (omega * b), 0.0)
+        for arr in (bx, by1, by2):
+            arr = arr[np.isfinite(arr)]
+            if arr.size:
+                bps.append(float(arr.max()))
+        s_sat = max(bps)
+        if dist(s_sat) <= r:
+            return objective(s_sat) / r
+    # bracket [s_lo, s_hi] with dist(s_lo) < r <= dist(s_hi), s_hi = 2 s_lo
+    s_hi = 1.0
+    if dist(s_hi) < r:
+        for _ in range(4000):
+            s_hi *= 2.0
+            if dist(s_hi) >= r:
+                break
+        s_lo = 0.5 * s_hi
+    else:
+        s_lo = 1.0
+        for _ in range(4000):
+            s_lo *= 0.5
+            if dist(s_lo) < r or s_lo == 0.0:
+                break
+        s_hi = 2.0 * s_lo
+    for _ in range(200):
+        if s_hi - s_lo <= 1e-14 * s_hi:
+            break
+        mid = 0.5 * (s_lo + s_hi)
+        if dist(mid) < r:
+            s_lo = mid
+        else:
+            s_hi = mid
+    return objective(s_hi) / r
+
+
+# ----------------------------------------------------------------------------
+# optimality measures on the unscaled LP (R10)
+# ----------------------------------------------------------------------------
+
+def kkt_stats(inst, A_orig, x, y):
+    """Residuals, objectives and gaps of (x, y) for the unscaled LP, with the reduced
+    costs r = proj_R(c - A'y) (Sec. 2, "natural choice").
+
+    primal residual  Ax - proj_[lc,uc](Ax)        relative: /(1 + ||Combine(lc,uc)||_2)
+    dual residual    (c - A'y) - r                relative: /(1 + ||c||_2)
+    pobj = c'x, dobj = lc'y^+ - uc'y^- + lv'r^+ - uv'r^- (Eq. (1) and App. D's expansion)
+    gap              |pobj - dobj| / (1 + |pobj| + |dobj|)
+    rel_kkt = max of the three; paper_gap = |pobj - dobj| / (|pobj| + |dobj|) (Eq. (8))."""
+    Ax = A_orig @ x
+    ATy = A_orig.T @ y
+    pres = Ax - proj_box(Ax, inst.lc, inst.uc)
+    g = inst.c - ATy
+    r = proj_R(g, inst.lv, inst.uv)
+    dres = g - r
+    pobj = float(np.dot(inst.c, x))
+    dobj = -p_fn(-y, inst.lc, inst.uc) - p_fn(-r, inst.lv, inst.uv)
+    p2 = norm2(pres)
+    d2 = norm2(dres)
+    eps_p = p2 / (1.0 + norm2(combine(inst.lc, inst.uc)))
+    eps_d = d2 / (1.0 + norm2(inst.c))
+    eps_g = abs(pobj - dobj) / (1.0 + abs(pobj) + abs(dobj))
+    den = abs(pobj) + abs(dobj)
+    paper_gap = abs(pobj - dobj) / den if den > 0 else 0.0
+    return dict(
+        primal_res_l2=p2,
+        dual_res_l2=d2,
+        primal_res_inf=float(np.max(np.abs(pres))) if pres.size else 0.0,
+        dual_res_inf=float(np.max(np.abs(dres))) if dres.size else 0.0,
+        pobj=pobj,
+        dobj=dobj,
+        rel_primal=eps_p,
+        rel_dual=eps_d,
+        rel_gap=eps_g,
+        rel_kkt=max(eps_p, eps_d, eps_g),
+        paper_gap=paper_gap,
+    )
+
+
+def converged(st, prm: Params):
+    if prm.termination_mode == 0:
+        return st["rel_kkt"] <= prm.eps_rel_kkt
+    return (st["primal_res_inf"] <= prm.eps_abs_feas and st["dual_res_inf"] <= prm.eps_abs_feas
+            and st["paper_gap"] <= prm.eps_rel_gap)
+
+
+# ----------------------------------------------------------------------------
+# PDLP (Algorithm 1)
+# ----------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Result:
+    status: int
+    x: np.ndarray
+    y: np.ndarray
+    stats: dict
+    trace: list
+
+
+def solve(inst, prm: Params | None = None, trace_iters: int = 0, lp: ScaledLP | None = None,
+          x_init=None, y_init=None) -> Result:
+    """Algorithm 1 after preconditioning.  ``trace_iters`` > 0 records, for each of the
+    first accepted iterations, the scaled iterate and the step/weight scalars.
+    ``x_init``/``y_init`` (scaled space) override R1's starting point."""
+    prm = prm or Params()
+    if lp is None:
+        lp = precondition(inst, prm.ruiz_iters, prm.pc_alpha)
+    m, n = inst.m, inst.n
+    maxabs = float(np.max(np.abs(lp.A.data))) if lp.A.nnz else 0.0
+    eta_hat = 1.0 / maxabs if maxabs > 0 else 1.0  # R2
+    if prm.fixed_step is not None:
+        eta_hat = prm.fixed_step
+    omega = initial_primal_weight(lp.c, lp.lc, lp.uc)
+    if prm.fixed_omega is not None:
+        omega = prm.fixed_omega
+    # R1
+    x = proj_box(np.zeros(n), lp.lv, lp.uv) if x_init is None else np.array(x_init, dtype=float)
+    y = np.zeros(m) if y_init is None else np.array(y_init, dtype=float)
+    Ax = lp.A @ x
+    ATy = lp.AT @ y
+    k = t = 0
+    n_outer = 0
+    x0, y0 = x.copy(), y.copy()  # z^{n,0}
+    mu_ref = None  # mu(z^{n,0}, z^{n-1,0})  (R5, R7)
+    mu_c_prev = math.inf  # R6
+    Sx, Sy, SAx, SATy, W = np.zeros(n), np.zeros(m), np.zeros(m), np.zeros(n), 0.0
+    stats = dict(iterations=0, attempts=0, rejected_steps=0, restarts=[0, 0, 0],
+                 kkt_passes=0.0)
+    trace = []
+
+    def unscale(xs, ys):
+        return lp.d2 * xs, lp.d1 * ys
+
+    def finish(status, xs, ys):
+        xu, yu = unscale(xs, ys)
+        st = kkt_stats(inst, lp.A_orig, xu, yu)
+        stats.update(st)
+        stats.update(iterations=k, omega=omega, eta_hat=eta_hat)
+        return Result(status, xu, yu, stats, trace)
+
+    # termination check before the first step (Sec. 3, "Periodic checks")
+    xu, yu = unscale(x, y)
+    if converged(kkt_stats(inst, lp.A_orig, xu, yu), prm):
+        return finish(OPTIMAL, x, y)
+
+    while True:
+        step_omega = omega
+        if prm.fixed_step is not None:
+            tau, sig = prm.fixed_step / omega, prm.fixed_step * omega
+            xn = primal_step(x, ATy, lp.c, lp.lv, lp.uv, tau)
+            Axn = lp.A @ xn
+            yn = dual_step(y, Ax, Axn, lp.lc, lp.uc, sig)
+            eta, eta_new, attempts, ok = prm.fixed_step, prm.fixed_step, 1, True
+        else:
+            xn, yn, Axn, eta, eta_new, attempts, ok = adaptive_step(
+                lp, x, y, Ax, ATy, omega, eta_hat, k, prm.max_step_retries)
+        stats["attempts"] += attempts
+        stats["rejected_steps"] += attempts - 1
+        stats["kkt_passes"] += 0.5 * attempts + 0.5
+        if not ok:
+            return finish(NUMERICAL_ERROR, x, y)
+        ATyn = lp.AT @ yn
+        # running weighted average since the last restart (Algorithm 1)
+        Sx += eta * xn
+        Sy += eta * yn
+        SAx += eta * Axn
+        SATy += eta * ATyn
+        W += eta
+        x, y, Ax, ATy = xn, yn, Axn, ATyn
+        eta_hat = eta_new
+        t += 1
+        k += 1
+        rec = None
+        if len(trace) < trace_iters:
+            rec = dict(k=k, x=x.copy(), y=y.copy(), eta=eta, omega=step_omega,
+                       eta_hat=eta_hat, attempts=attempts, restart=RESTART_NONE,
+                       mu_cur=math.nan, mu_avg=math.nan)
+            trace.append(rec)
+
+        is_check = (k % prm.check_period) == 0  # R4
+        is_art = prm.restarts and (t >= prm.beta_art * k)
+        is_limit = k >= prm.max_iters
+        if not (is_check or is_art or is_limit):
+            continue
+        # GetRestartCandidate (Sec. 3): current iterate vs the average (R8, R18)
+        xa, ya, Axa, ATya = Sx / W, Sy / W, SAx / W, SATy / W
+        mu_cur = normalized_gap(lp, x, y, Ax, ATy, x0, y0, omega)
+        mu_avg = normalized_gap(lp, xa, ya, Axa, ATya, x0, y0, omega)
+        if mu_cur < mu_avg:
+            cand, mu_c = (x, y, Ax, ATy), mu_cur
+        else:
+            cand, mu_c = (xa, ya, Axa, ATya), mu_avg
+        if rec is not None:
+            rec["mu_cur"], rec["mu_avg"] = mu_cur, mu_avg
+        if is_check or is_limit:  # R9
+            xu, yu = unscale(cand[0], cand[1])
+            if converged(kkt_stats(inst, lp.A_orig, xu, yu), prm):
+                return finish(OPTIMAL, cand[0], cand[1])
+            if is_limit:
+                return finish(ITERATION_LIMIT, cand[0], cand[1])
+        kind = RESTART_NONE
+        if prm.restarts and is_check and mu_ref is not None:
+            if mu_c <= prm.beta_suff * mu_ref:
+                kind = RESTART_SUFFICIENT
+            elif mu_c <= prm.beta_nec * mu_ref and mu_c > mu_c_prev:
+                kind = RESTART_NECESSARY
+        if kind == RESTART_NONE and is_art:
+            kind = RESTART_ARTIFICIAL
+        if is_check:
+            mu_c_prev = mu_c
+        if kind == RESTART_NONE:
+            continue
+        # restart the outer loop: z^{n+1,0} <- candidate, eta_hat carried
+        stats["restarts"][kind - 1] += 1
+        if rec is not None:
+            rec["restart"] = kind
+        x, y, Ax, ATy = (v.copy() for v in cand)
+        if prm.fixed_omega is None:
+            omega = primal_weight_update(x, y, x0, y0, omega, prm.theta, prm.eps_zero)
+        mu_ref = normalized_gap(lp, x, y, Ax, ATy, x0, y0, omega)  # R7
+        x0, y0 = x.copy(), y.copy()
+        n_outer += 1
+        t = 0
+        mu_c_prev = math.inf
+        Sx, Sy, SAx, SATy, W = np.zeros(n), np.zeros(m), np.zeros(m), np.zeros(n), 0.0

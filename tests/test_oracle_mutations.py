@@ -1,0 +1,72 @@
+"""Planted mistakes in the oracle (on the CPU, via monkeypatch) must be caught by the
+pins: a dropped term, a wrong sign, a swapped operand.  Each test plants one mistake
+and asserts that the corresponding pin then fails."""
+import math
+
+import numpy as np
+import pytest
+
+import lpgen
+from oracle import pdlp_oracle as O
+from tests import test_oracle_pins as P
+
+
+def test_dual_step_sign_error_is_caught(monkeypatch):
+    def bad(y, Ax, Ax_new, lc, uc, sigma):
+        yhat = y + sigma * (2.0 * Ax_new - Ax)  # wrong sign
+        return yhat - O.proj_box(yhat, -sigma * uc, -sigma * lc)
+    monkeypatch.setattr(O, "dual_step", bad)
+    with pytest.raises(AssertionError):
+        P.test_dual_step_equals_prox_argmin()
+
+
+def test_dual_step_dropped_extrapolation_is_caught(monkeypatch):
+    def bad(y, Ax, Ax_new, lc, uc, sigma):
+        yhat = y - sigma * Ax_new  # A x' instead of A(2x' - x)
+        return yhat - O.proj_box(yhat, -sigma * uc, -sigma * lc)
+    monkeypatch.setattr(O, "dual_step", bad)
+    with pytest.raises(AssertionError):
+        P.test_fixed_step_iterates_equal_chambolle_pock()
+
+
+def test_normalized_gap_dropped_dual_term_is_caught(monkeypatch):
+    orig = O.normalized_gap
+
+    def bad(lp, x, y, Ax, ATy, x_ref, y_ref, omega):
+        # forget the row terms: evaluate with every row free (y part fixed at 0 move)
+        lp2 = O.ScaledLP(**{**lp.__dict__, "lc": np.full_like(lp.lc, -np.inf),
+                            "uc": np.full_like(lp.uc, np.inf)})
+        return orig(lp2, x, np.zeros_like(y), Ax, ATy, x_ref, y_ref, omega)
+    monkeypatch.setattr(O, "normalized_gap", bad)
+    with pytest.raises(AssertionError):
+        P.test_normalized_gap_vs_sorted_breakpoints(0)
+
+
+def test_primal_weight_inverted_ratio_is_caught(monkeypatch):
+    def bad(x_new, y_new, x_old, y_old, omega, theta=0.5, eps_zero=1e-10):
+        dx = O.norm2(x_new - x_old)
+        dy = O.norm2(y_new - y_old)
+        return math.exp(theta * math.log(dx / dy) + (1 - theta) * math.log(omega))
+    monkeypatch.setattr(O, "primal_weight_update", bad)
+    with pytest.raises(AssertionError):
+        P.test_primal_weight_closed_form()
+
+
+def test_pc_row_col_swap_is_caught(monkeypatch):
+    orig = O._row_pnorm
+
+    def bad(M, p):
+        return orig(M, 2.0 if p == 1.0 else p)  # l2 instead of l1
+    monkeypatch.setattr(O, "_row_pnorm", bad)
+    with pytest.raises(AssertionError):
+        P.test_pock_chambolle_alpha1_row_col_l1()
+
+
+def test_dual_objective_swapped_bounds_is_caught(monkeypatch):
+    orig = O.p_fn
+
+    def bad(y, lo, hi):
+        return orig(y, hi, lo)  # lower and upper bound swapped in p(y; l, u)
+    monkeypatch.setattr(O, "p_fn", bad)
+    with pytest.raises(AssertionError):
+        P.test_weak_duality_any_dual_point()

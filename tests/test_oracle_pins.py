@@ -1,0 +1,481 @@
+"""Pins of the CPU oracle against things other than itself: closed forms, brute force,
+a second library solver, textbook operators, invariants the paper states.
+
+Each test names the passage of the paper it checks.  All run on the CPU.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.optimize as so
+import scipy.sparse as sp
+
+import lpgen
+from oracle import pdlp_oracle as O
+from tests import lp_helpers as H
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _highs(inst):
+    A = inst.scipy_csr().toarray()
+    rows_ub, rhs_ub, rows_eq, rhs_eq = [], [], [], []
+    for i in range(inst.m):
+        if inst.lc[i] == inst.uc[i]:
+            rows_eq.append(A[i]); rhs_eq.append(inst.lc[i])
+            continue
+        if np.isfinite(inst.uc[i]):
+            rows_ub.append(A[i]); rhs_ub.append(inst.uc[i])
+        if np.isfinite(inst.lc[i]):
+            rows_ub.append(-A[i]); rhs_ub.append(-inst.lc[i])
+    bounds = [(None if not np.isfinite(l) else l, None if not np.isfinite(u) else u)
+              for l, u in zip(inst.lv, inst.uv)]
+    r = so.linprog(inst.c, A_ub=np.array(rows_ub) if rows_ub else None,
+                   b_ub=np.array(rhs_ub) if rhs_ub else None,
+                   A_eq=np.array(rows_eq) if rows_eq else None,
+                   b_eq=np.array(rhs_eq) if rhs_eq else None, bounds=bounds, method="highs")
+    assert r.status == 0
+    return r.fun
+
+
+# ---------------------------------------------------------------------------
+# whole solve: closed forms, brute force, a second solver
+# ---------------------------------------------------------------------------
+
+def test_box_only_closed_form():
+    """m = 0 (Eq. (1) without rows): x_i = lv_i if c_i > 0 else uv_i."""
+    rng = np.random.default_rng(1)
+    n = 50
+    lv = rng.uniform(-5, 0, n)
+    uv = lv + rng.uniform(0.5, 3, n)
+    c = rng.uniform(-1, 1, n)
+    inst = H.make_lp(np.zeros((0, n)), c, [], [], lv, uv)
+    res = O.solve(inst, O.Params(eps_rel_kkt=1e-12))
+    assert res.status == O.OPTIMAL
+    x_star = np.where(c > 0, lv, uv)
+    np.testing.assert_allclose(res.x, x_star, rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_bruteforce_vertices_and_highs(seed):
+    """Small two-sided LPs (n <= 5): PDLP's objective equals the best vertex (Eq. (1))
+    and scipy-HiGHS's optimum."""
+    rng = np.random.default_rng(100 + seed)
+    m, n = int(rng.integers(2, 5)), int(rng.integers(2, 6))
+    inst = H.random_bounded_lp(rng, m, n)
+    best, _ = H.brute_force_vertices(inst)
+    res = O.solve(inst, O.Params(eps_rel_kkt=1e-10, max_iters=200000))
+    assert res.status == O.OPTIMAL
+    assert abs(res.stats["pobj"] - best) <= 1e-6 * (1 + abs(best))
+    assert abs(_highs(inst) - best) <= 1e-7 * (1 + abs(best))
+
+
+def test_diagonal_closed_form():
+    """Diagonal A: every coordinate decouples; x_j* is the end of
+    [max(lv, lc/a), min(uv, uc/a)] that c_j points to (Eq. (1))."""
+    rng = np.random.default_rng(7)
+    n = 300
+    a = rng.uniform(0.5, 3.0, n) * np.where(rng.random(n) < 0.5, -1, 1)
+    lv, uv = np.full(n, -2.0), np.full(n, 2.0)
+    t_lo = rng.uniform(-1.5, 0.0, n)
+    t_hi = t_lo + rng.uniform(0.2, 1.0, n)
+    lc = np.where(a > 0, a * t_lo, a * t_hi)
+    uc = np.where(a > 0, a * t_hi, a * t_lo)
+    c = rng.uniform(-1, 1, n)
+    inst = H.make_lp(np.diag(a), c, lc, uc, lv, uv)
+    res = O.solve(inst, O.Params(eps_rel_kkt=1e-11, max_iters=100000))
+    assert res.status == O.OPTIMAL
+    x_star = np.where(c > 0, np.maximum(lv, t_lo), np.minimum(uv, t_hi))
+    np.testing.assert_allclose(res.x, x_star, atol=1e-7)
+
+
+def test_continuous_knapsack_closed_form():
+    """One equality row sum a_i x_i = b, 0 <= x <= u: greedy fill by c_i/a_i."""
+    rng = np.random.default_rng(11)
+    n = 40
+    a = rng.uniform(0.5, 2.0, n)
+    u = rng.uniform(0.5, 2.0, n)
+    c = rng.uniform(-1, 1, n)
+    b = 0.4 * float(a @ u)
+    inst = H.make_lp(a[None, :], c, [b], [b], np.zeros(n), u)
+    res = O.solve(inst, O.Params(eps_rel_kkt=1e-11, max_iters=200000))
+    assert res.status == O.OPTIMAL
+    order = np.argsort(c / a)
+    x = np.zeros(n)
+    left = b
+    for j in order:
+        take = min(u[j], left / a[j])
+        x[j] = take
+        left -= take * a[j]
+        if left <= 0:
+            break
+    assert abs(res.stats["pobj"] - c @ x) <= 1e-7 * (1 + abs(c @ x))
+
+
+def test_golden_textbook_lp():
+    """A hand-solved two-variable LP (Eq. (1)); primal and dual optimum derived by hand
+    in the fixture."""
+    with open(os.path.join(GOLDEN, "textbook_lp.json")) as f:
+        g = json.load(f)
+    inf = float("inf")
+    conv = lambda v: [inf if s == "inf" else (-inf if s == "-inf" else s) for s in v]  # noqa
+    inst = H.make_lp(g["A"], g["c"], conv(g["lc"]), conv(g["uc"]), conv(g["lv"]), conv(g["uv"]))
+    res = O.solve(inst, O.Params(eps_rel_kkt=1e-12, max_iters=100000))
+    assert res.status == O.OPTIMAL
+    np.testing.assert_allclose(res.x, g["x_star"], atol=1e-8)
+    np.testing.assert_allclose(res.y, g["y_star"], atol=1e-8)
+    assert abs(res.stats["pobj"] - g["obj"]) < 1e-8
+
+
+def test_config0_matches_highs_and_kkt():
+    """The small random LP reaches relative KKT 1e-8; objective equals HiGHS's; the
+    residuals and the gap vanish (Sec. 7 termination quantities)."""
+    inst = lpgen.config0()
+    res = O.solve(inst, O.Params())
+    assert res.status == O.OPTIMAL
+    st = res.stats
+    assert st["rel_kkt"] <= 1e-8
+    ref = _highs(inst)
+    assert abs(st["pobj"] - ref) <= 1e-6 * abs(ref)
+
+
+def test_weak_duality_any_dual_point():
+    """For a primal-feasible x and any y in Y with r = proj_R(c - A'y), the dual
+    objective lc'y+ - uc'y- + lv'r+ - uv'r- never exceeds c'x when c - A'y - r = 0
+    (Eq. (1)); with every variable boxed R is all of R^n, so any y in Y qualifies."""
+    inst = lpgen.config0()
+    A = inst.scipy_csr()
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        y = rng.standard_normal(inst.m) * 3
+        y = np.where(~np.isfinite(inst.lc) & (y > 0), 0.0, y)
+        st = O.kkt_stats(inst, A, inst.x0, y)
+        assert st["dual_res_l2"] == 0.0
+        assert st["dobj"] <= st["pobj"] + 1e-9
+        assert st["primal_res_l2"] <= 1e-9
+
+
+def test_scaled_and_unscaled_same_objective():
+    """Preconditioning changes the iterates, not the LP (Sec. 3): with and without it
+    the objective agrees."""
+    inst = lpgen.random_lp(60, 120, 4, seed=5)
+    a = O.solve(inst, O.Params(eps_rel_kkt=1e-9, max_iters=300000))
+    b = O.solve(inst, O.Params(eps_rel_kkt=1e-9, ruiz_iters=0, pc_alpha=0.0, max_iters=300000))
+    assert a.status == O.OPTIMAL and b.status == O.OPTIMAL
+    assert abs(a.stats["pobj"] - b.stats["pobj"]) <= 1e-6 * (1 + abs(a.stats["pobj"]))
+
+
+# ---------------------------------------------------------------------------
+# the PDHG step (Eq. (3), App. B)
+# ---------------------------------------------------------------------------
+
+def _rand_bounds(rng, m):
+    lc = rng.standard_normal(m)
+    uc = lc + rng.uniform(0, 2, m)
+    kind = rng.integers(0, 5, m)
+    lc = np.where(kind == 1, -np.inf, lc)
+    uc = np.where(kind == 2, np.inf, uc)
+    lc = np.where(kind == 3, -np.inf, lc)
+    uc = np.where(kind == 3, np.inf, uc)
+    uc = np.where(kind == 4, lc, uc)
+    return lc, uc
+
+
+def test_dual_step_equals_prox_argmin():
+    """Eq. (3b) equals the PDHG dual step of App. B written as an explicit argmin of
+    p(y; -uc, -lc) + ||y - (y_k - sigma A(2x'-x))||^2 / (2 sigma) over Y."""
+    rng = np.random.default_rng(4)
+    m = 400
+    lc, uc = _rand_bounds(rng, m)
+    for sigma in (0.01, 0.7, 5.0):
+        y = rng.standard_normal(m)
+        y = np.where(~np.isfinite(lc) & (y > 0), -y, y)
+        y = np.where(~np.isfinite(uc) & (y < 0), -y, y)
+        y = np.where(~np.isfinite(lc) & ~np.isfinite(uc), 0.0, y)
+        Ax = rng.standard_normal(m)
+        Axn = rng.standard_normal(m)
+        got = O.dual_step(y, Ax, Axn, lc, uc, sigma)
+        v = y - sigma * (2 * Axn - Ax)
+        want = H.prox_p_argmin(v, sigma, lc, uc)
+        np.testing.assert_allclose(got, want, rtol=1e-14, atol=1e-14 * np.abs(v).max())
+
+
+def test_dual_step_literal_formula():
+    """The evaluation order of R17 agrees with Eq. (3b) as printed,
+    y - sigma q - sigma proj_[-uc,-lc](y/sigma - q), to rounding."""
+    rng = np.random.default_rng(5)
+    m = 1000
+    lc, uc = _rand_bounds(rng, m)
+    y = np.zeros(m)
+    Ax = rng.standard_normal(m)
+    Axn = rng.standard_normal(m)
+    sigma = 0.37
+    q = 2 * Axn - Ax
+    lit = y - sigma * q - sigma * np.clip(y / sigma - q, -uc, -lc)
+    got = O.dual_step(y, Ax, Axn, lc, uc, sigma)
+    np.testing.assert_allclose(got, lit, rtol=1e-13, atol=1e-15)
+
+
+def test_fixed_step_iterates_equal_chambolle_pock():
+    """With restarts off and eta, omega fixed, PDLP's iterates are textbook PDHG
+    (Chambolle-Pock with K = -A, App. B), dual prox as an explicit argmin."""
+    inst = lpgen.random_lp(30, 50, 3, seed=9)
+    prm = O.Params(ruiz_iters=0, pc_alpha=0.0, fixed_step=0.2, fixed_omega=1.3, restarts=False,
+                   max_iters=40, eps_rel_kkt=0.0)
+    res = O.solve(inst, prm, trace_iters=40)
+    A = inst.scipy_csr()
+    tau, sigma = 0.2 / 1.3, 0.2 * 1.3
+    x = np.clip(np.zeros(inst.n), inst.lv, inst.uv)
+    y = np.zeros(inst.m)
+    for rec in res.trace:
+        xn = np.clip(x - tau * (inst.c - A.T @ y), inst.lv, inst.uv)
+        v = y - sigma * (A @ (2 * xn - x))
+        yn = H.prox_p_argmin(v, sigma, inst.lc, inst.uc)
+        np.testing.assert_allclose(rec["x"], xn, atol=1e-11)
+        np.testing.assert_allclose(rec["y"], yn, atol=1e-11)
+        x, y = xn, yn
+
+
+def test_iterates_stay_in_X_and_Y_exactly():
+    """Sec. 2's case analysis: y^{k+1} in Y and x^{k+1} in X, bit for bit, for every
+    iterate (free rows keep y_i = 0 exactly)."""
+    inst = lpgen.random_lp(80, 160, 4, seed=12)
+    inst.lc[:10] = -np.inf
+    inst.uc[10:20] = np.inf
+    inst.lc[20:25] = -np.inf
+    inst.uc[20:25] = np.inf
+    lp = O.precondition(inst)
+    res = O.solve(inst, O.Params(max_iters=300), trace_iters=300, lp=lp)
+    for rec in res.trace:
+        x, y = rec["x"], rec["y"]
+        assert np.all(x >= lp.lv) and np.all(x <= lp.uv)
+        assert np.all(y[:10] <= 0)
+        assert np.all(y[10:20] >= 0)
+        assert np.all(y[20:25] == 0)
+
+
+def test_step_size_bound_and_acceptance():
+    """Algorithm 2: the accepted eta satisfies Eq. (5), and eta_bar >= 1/||A||_2
+    (Sec. 3, "Step size choice"), ||A||_2 from a dense SVD."""
+    inst = lpgen.random_lp(40, 70, 4, seed=13)
+    lp = O.precondition(inst)
+    Ad = lp.A.toarray()
+    nrm = np.linalg.svd(Ad, compute_uv=False)[0]
+    rng = np.random.default_rng(14)
+    for trial in range(30):
+        x = np.clip(rng.standard_normal(inst.n) * 3, lp.lv, lp.uv)
+        y = rng.standard_normal(inst.m)
+        Ax, ATy = Ad @ x, Ad.T @ y
+        omega = float(np.exp(rng.uniform(-2, 2)))
+        for eta in (0.01, 1.0, 10.0):
+            xn = O.primal_step(x, ATy, lp.c, lp.lv, lp.uv, eta / omega)
+            yn = O.dual_step(y, Ax, Ad @ xn, lp.lc, lp.uc, eta * omega)
+            dx, dy = xn - x, yn - y
+            inter = abs(dy @ (Ad @ dx))
+            if inter > 0:
+                eta_bar = (omega * dx @ dx + dy @ dy / omega) / (2 * inter)
+                assert eta_bar >= (1 - 1e-12) / nrm
+        xo, yo, Axo, eta_acc, eta_new, att, ok = O.adaptive_step(
+            lp, x, y, Ax, ATy, omega, 50.0, trial, 60)
+        assert ok
+        dx, dy = xo - x, yo - y
+        inter = abs(dy @ (Axo - Ax))
+        if inter > 0:
+            assert eta_acc <= (omega * dx @ dx + dy @ dy / omega) / (2 * inter) * (1 + 1e-12)
+        assert eta_new <= (1 + (trial + 2) ** -0.6) * eta_acc * (1 + 1e-15)
+
+
+def test_running_average_and_linearity():
+    """The weighted average since the last restart (Algorithm 1) equals the directly
+    weighted mean of the traced iterates, and A x_bar from the running sums equals
+    A (x_bar) (linearity, R18)."""
+    inst = lpgen.random_lp(50, 90, 4, seed=15)
+    lp = O.precondition(inst)
+    res = O.solve(inst, O.Params(max_iters=60, restarts=False, eps_rel_kkt=0.0),
+                  trace_iters=60, lp=lp)
+    xs = np.array([r["x"] for r in res.trace])
+    ys = np.array([r["y"] for r in res.trace])
+    w = np.array([r["eta"] for r in res.trace])
+    xbar = (w[:, None] * xs).sum(0) / w.sum()
+    Axbar_sum = (w[:, None] * np.array([lp.A @ v for v in xs])).sum(0) / w.sum()
+    np.testing.assert_allclose(lp.A @ xbar, Axbar_sum, atol=1e-12 * (1 + np.abs(Axbar_sum).max()))
+    ybar = (w[:, None] * ys).sum(0) / w.sum()
+    assert np.all(np.isfinite(ybar))
+
+
+# ---------------------------------------------------------------------------
+# normalized duality gap (Sec. 3, "Adaptive restarts")
+# ---------------------------------------------------------------------------
+
+def _rand_point(rng, lp, scale=1.0):
+    with np.errstate(invalid="ignore"):
+        x = np.clip(lp.lv + (lp.uv - lp.lv) * rng.random(lp.c.shape[0]), lp.lv, lp.uv)
+    x = np.where(np.isfinite(x), x, rng.standard_normal(x.shape[0]))
+    y = rng.standard_normal(lp.lc.shape[0]) * scale
+    y = np.where(~np.isfinite(lp.lc) & (y > 0), -y, y)
+    y = np.where(~np.isfinite(lp.uc) & (y < 0), -y, y)
+    y = np.where(~np.isfinite(lp.lc) & ~np.isfinite(lp.uc), 0.0, y)
+    return x, y
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_normalized_gap_vs_sorted_breakpoints(seed):
+    """Bisection on the ball multiplier (oracle) vs an exact solve over sorted
+    breakpoints with the Lagrangian evaluated from Eq. (2) (helper)."""
+    rng = np.random.default_rng(200 + seed)
+    inst = lpgen.random_lp(25, 40, 3, seed=300 + seed, free_frac=0.1)
+    inst.lc[:4] = -np.inf
+    inst.uc[4:8] = np.inf
+    lp = O.precondition(inst)
+    for _ in range(3):
+        x, y = _rand_point(rng, lp)
+        xr, yr = _rand_point(rng, lp)
+        omega = float(np.exp(rng.uniform(-1, 1)))
+        Ax, ATy = lp.A @ x, lp.AT @ y
+        got = O.normalized_gap(lp, x, y, Ax, ATy, xr, yr, omega)
+        want = H.exact_normalized_gap(lp, x, y, Ax, ATy, xr, yr, omega)
+        assert abs(got - want) <= 1e-8 * (1 + abs(want))
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_normalized_gap_vs_sampling_tiny(case):
+    """n + m <= 3: the trust-region maximum is at least every sampled feasible value
+    in the ball, and sampling gets within a small margin of it."""
+    rng = np.random.default_rng(500 + case)
+    m, n = (1, 1) if case < 2 else (1, 2)
+    A = rng.standard_normal((m, n))
+    lc = np.array([-0.5]) if case != 1 else np.array([-np.inf])
+    uc = np.array([0.8])
+    inst = H.make_lp(A, rng.uniform(-1, 1, n), lc, uc, np.full(n, -1.0), np.full(n, 1.5))
+    lp = O.precondition(inst, ruiz_iters=0, pc_alpha=0.0)
+    x, y = _rand_point(rng, lp)
+    xr, yr = _rand_point(rng, lp)
+    omega = 0.8
+    Ad = lp.A.toarray()
+    Ax, ATy = Ad @ x, Ad.T @ y
+    mu = O.normalized_gap(lp, x, y, Ax, ATy, xr, yr, omega)
+    r = math.sqrt(omega * np.sum((x - xr) ** 2) + np.sum((y - yr) ** 2) / omega)
+    best = H.sample_trust_region_max(lp, x, y, Ad, r, omega, rng)
+    assert mu * r >= best - 1e-9
+    assert mu * r <= best + 0.02 * (abs(best) + r)
+
+
+def test_normalized_gap_zero_at_optimum():
+    """rho_r(z) = 0 iff z is optimal (Sec. 3): tiny at a tightly converged point,
+    clearly positive at the starting point."""
+    inst = lpgen.random_lp(30, 60, 3, seed=21)
+    lp = O.precondition(inst)
+    res = O.solve(inst, O.Params(eps_rel_kkt=1e-12, max_iters=400000), lp=lp)
+    assert res.status == O.OPTIMAL
+    xs, ys = res.x / lp.d2, res.y / lp.d1
+    Ax, ATy = lp.A @ xs, lp.AT @ ys
+    rng = np.random.default_rng(22)
+    xr, yr = _rand_point(rng, lp)
+    mu_opt = O.normalized_gap(lp, xs, ys, Ax, ATy, xr, yr, 1.0)
+    x0 = np.clip(np.zeros(inst.n), lp.lv, lp.uv)
+    mu_0 = O.normalized_gap(lp, x0, np.zeros(inst.m), lp.A @ x0, np.zeros(inst.n), xr, yr, 1.0)
+    assert abs(mu_opt) < 1e-6
+    assert mu_0 > 1e-2
+
+
+def test_normalized_gap_ball_inactive_is_duality_gap():
+    """When every direction saturates inside the ball, r*rho_r(z) is the plain
+    duality gap max_{zh in Z} L(x,yh) - L(xh,y): for boxed x it is attained at the box
+    corner against g, and for rows with lc <= (Ax)_i <= uc every row term peaks at 0."""
+    rng = np.random.default_rng(23)
+    m, n = 6, 9
+    A = rng.standard_normal((m, n))
+    x = rng.uniform(-1, 1, n)
+    ax = A @ x
+    lc = ax - rng.uniform(1, 2, m)
+    uc = ax + rng.uniform(1, 2, m)
+    lc[:3] = -np.inf  # rows with yh <= 0 only
+    inst = H.make_lp(A, rng.uniform(-1, 1, n), lc, uc, np.full(n, -1.0), np.full(n, 1.0))
+    lp = O.precondition(inst, ruiz_iters=0, pc_alpha=0.0)
+    y = rng.standard_normal(m)
+    y[:3] = -np.abs(y[:3])
+    Ad = lp.A.toarray()
+    Ax, ATy = Ad @ x, Ad.T @ y
+    g = lp.c - ATy
+    xr = x + 1e6  # reference far away: the ball contains everything reachable
+    yr = y
+    omega = 1.0
+    r = math.sqrt(omega * np.sum((x - xr) ** 2) + np.sum((y - yr) ** 2) / omega)
+    mu = O.normalized_gap(lp, x, y, Ax, ATy, xr, yr, omega)
+    xh = np.where(g > 0, lp.lv, np.where(g < 0, lp.uv, x))
+    yh = np.zeros(m)
+    gap = H.lagrangian(lp, x, yh, lambda v: Ad @ v) - H.lagrangian(lp, xh, y, lambda v: Ad @ v)
+    assert gap > 0
+    assert abs(mu * r - gap) <= 1e-9 * (1 + abs(gap))
+
+
+# ---------------------------------------------------------------------------
+# preconditioning, primal weight
+# ---------------------------------------------------------------------------
+
+def test_ruiz_norms_go_to_one():
+    """Ruiz (Sec. 3): applied iteratively, every row and column infinity norm tends
+    to 1."""
+    inst = lpgen.config1(scale=0.001)
+    lp = O.precondition(inst, ruiz_iters=60, pc_alpha=0.0)
+    A = abs(lp.A)
+    rmax = A.max(axis=1).toarray().ravel()
+    cmax = A.max(axis=0).toarray().ravel()
+    assert np.all(np.abs(rmax[rmax > 0] - 1) < 1e-3)
+    assert np.all(np.abs(cmax[cmax > 0] - 1) < 1e-3)
+    # and the scaled matrix is D1 A D2 exactly as recorded
+    A0 = inst.scipy_csr()
+    D = sp.diags(lp.d1) @ A0 @ sp.diags(lp.d2)
+    np.testing.assert_allclose(D.toarray() if D.shape[0] < 3000 else D.data,
+                               lp.A.toarray() if D.shape[0] < 3000 else lp.A.data, rtol=1e-12)
+
+
+def test_pock_chambolle_alpha1_row_col_l1():
+    """Pock-Chambolle with alpha = 1 alone: row and column l1 norms of D1 A D2 with
+    D1 = 1/sqrt(row l1), D2 = 1/sqrt(col l1), checked on a dense matrix."""
+    rng = np.random.default_rng(24)
+    Ad = rng.standard_normal((7, 5))
+    Ad[2] = 0
+    inst = H.make_lp(Ad, np.ones(5), -np.ones(7), np.ones(7), np.zeros(5), np.ones(5))
+    lp = O.precondition(inst, ruiz_iters=0, pc_alpha=1.0)
+    r = np.abs(Ad).sum(1)
+    c = np.abs(Ad).sum(0)
+    d1 = np.where(r > 0, 1 / np.sqrt(r), 1.0)
+    d2 = 1 / np.sqrt(c)
+    np.testing.assert_allclose(lp.d1, d1, rtol=1e-15)
+    np.testing.assert_allclose(lp.d2, d2, rtol=1e-15)
+    np.testing.assert_allclose(lp.A.toarray(), d1[:, None] * Ad * d2[None, :], rtol=1e-14)
+    assert lp.lv[0] == 0 and lp.uv[0] == pytest.approx(1 / d2[0], rel=1e-15)
+
+
+def test_primal_weight_closed_form():
+    """Algorithm 3 with theta = 1/2 is the geometric mean of omega and Dy/Dx; outside
+    (eps0, 1/eps0) the weight is kept."""
+    rng = np.random.default_rng(25)
+    for _ in range(20):
+        xo, yo = rng.standard_normal(5), rng.standard_normal(4)
+        xn, yn = xo + rng.standard_normal(5), yo + rng.standard_normal(4)
+        om = float(np.exp(rng.uniform(-3, 3)))
+        dx, dy = np.linalg.norm(xn - xo), np.linalg.norm(yn - yo)
+        assert abs(O.primal_weight_update(xn, yn, xo, yo, om) - math.sqrt(om * dy / dx)) \
+            <= 1e-13 * math.sqrt(om * dy / dx)
+    assert O.primal_weight_update(np.ones(3), np.ones(2), np.ones(3), np.zeros(2), 2.5) == 2.5
+    assert O.primal_weight_update(np.ones(3) * 1e11, np.ones(2), np.zeros(3), np.zeros(2), 2.5) == 2.5
+
+
+def test_initial_primal_weight_and_combine():
+    """InitializePrimalWeight and Combine (Sec. 3) on a hand example."""
+    lc = np.array([-np.inf, -3.0, 2.0, -np.inf])
+    uc = np.array([4.0, 1.0, np.inf, np.inf])
+    np.testing.assert_array_equal(O.combine(lc, uc), [4.0, 3.0, 2.0, 0.0])
+    c = np.array([3.0, 4.0])
+    assert O.initial_primal_weight(c, lc, uc) == pytest.approx(5.0 / math.sqrt(29.0), rel=1e-15)
+    assert O.initial_primal_weight(np.zeros(2), lc, uc) == 1.0
+
+
+def test_step_factors_first_step_positive():
+    """Algorithm 2's reduction factor must be positive at the first step (R3)."""
+    red, grow = O.step_factors(0)
+    assert red == pytest.approx(1 - 2 ** -0.3) and grow == pytest.approx(1 + 2 ** -0.6)
