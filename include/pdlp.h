@@ -1,0 +1,172 @@
+/*
+ * pdlp.h -- C ABI of the GB300 (sm_103a) implementation of PDLP, the restarted
+ * primal-dual hybrid gradient method for linear programming of
+ * "PDLP: A Practical First-Order Method for Large-Scale Linear Programming".
+ *
+ * Problem (Sec. 2, Eq. (1)):
+ *     minimize c'x   subject to   lc <= A x <= uc,   lv <= x <= uv,
+ * with A in R^{m x n} given in CSR form, bounds in R u {-inf, +inf} (IEEE
+ * +-INFINITY marks a missing bound).  The dual multipliers y (one per row) follow
+ * the sign convention of Eq. (1): y_i >= 0 on a row with only a finite lower bound,
+ * y_i <= 0 with only a finite upper bound, y_i = 0 on a free row.
+ *
+ * Conventions for every entry point:
+ *   - All arrays are owned by the caller; the library neither frees nor retains
+ *     them after the call returns.  The library allocates its own device work
+ *     memory (cudaMalloc) for the duration of a call and frees it before returning.
+ *   - params->inputs_on_device selects where the input AND output arrays live:
+ *     0 = host memory (pageable or pinned), 1 = device memory of the current CUDA
+ *     device.  Device arrays must not be written by other work while the call runs.
+ *   - params->cuda_stream (a cudaStream_t, may be NULL) is the stream all device work
+ *     is ordered on; the call blocks until its results are complete.
+ *   - Return value: 0 on success (for pdlp_solve: status OPTIMAL), a positive status
+ *     for a finished solve that did not reach the tolerance, a negative code for an
+ *     error, in which case outputs are not written and pdlp_last_error() describes
+ *     the failure.  No C++ exception crosses this interface.
+ *   - Every entry point is thread-compatible: concurrent calls need distinct
+ *     streams and output buffers; the only global state is the thread-local error
+ *     string.
+ */
+#ifndef PDLP_H_
+#define PDLP_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status and error codes ------------------------------------------------ */
+#define PDLP_OPTIMAL 0            /* termination criterion met                    */
+#define PDLP_ITERATION_LIMIT 1    /* params->max_iters accepted iterations done   */
+#define PDLP_TIME_LIMIT 2         /* params->time_limit_s exceeded                */
+#define PDLP_PRIMAL_INFEASIBLE 3  /* reserved (infeasibility certificate, App. D) */
+#define PDLP_DUAL_INFEASIBLE 4    /* reserved (infeasibility certificate, App. D) */
+#define PDLP_NUMERICAL_ERROR 5    /* non-finite step or step-retry cap reached    */
+#define PDLP_INVALID_ARGUMENT (-1)
+#define PDLP_OUT_OF_MEMORY (-2)
+#define PDLP_CUDA_ERROR (-3)
+
+/* precision of the bulk data (matrix values, iterates, SpMV accumulation) */
+#define PDLP_FP64 0
+#define PDLP_FP32_BULK 1
+
+/* Constraint matrix in CSR form (Sec. 5 "Multithreading": A x and A'y are the two
+ * sparse products of every iteration; this library builds the transpose itself).
+ *   row_ptr[m+1]: row_ptr[0] = 0, nondecreasing, row_ptr[m] = nnz.
+ *   col_idx[nnz]: strictly increasing within a row, 0 <= col < n.
+ *   val[nnz]:     finite.                                                        */
+typedef struct {
+  int64_t nnz;
+  const int64_t* row_ptr;
+  const int32_t* col_idx;
+  const double* val;
+} pdlp_csr;
+
+/* Algorithm parameters.  pdlp_params_default() fills the paper's defaults. */
+typedef struct {
+  double eps_rel_kkt;      /* termination_mode 0: stop when the relative KKT error
+                              (max of relative primal residual, relative dual
+                              residual, relative gap; all on the unscaled LP) is
+                              <= this.  Default 1e-8.                               */
+  int termination_mode;    /* 0: relative KKT; 1: Sec. 7 / Eq. (9): l_inf primal and
+                              dual residual <= eps_abs_feas and the relative gap of
+                              Eq. (8) <= eps_rel_gap.                               */
+  double eps_abs_feas;     /* default 1e-8                                          */
+  double eps_rel_gap;      /* default 1e-2                                          */
+  int64_t max_iters;       /* accepted PDHG iterations; default 1e9                  */
+  double time_limit_s;     /* wall-clock limit of the solve; default +inf            */
+  int ruiz_iters;          /* Sec. 3 "Diagonal Preconditioning": default 10          */
+  double pc_alpha;         /* Pock-Chambolle alpha in (0,2); <= 0 disables; default 1 */
+  int check_period;        /* restart/termination evaluation period (Sec. 3); 64    */
+  double beta_suff, beta_nec, beta_art; /* restart criteria (i)-(iii): 0.1, 0.9, 0.5 */
+  double theta;            /* primal weight smoothing (Algorithm 3): 0.5             */
+  double eps_zero;         /* Algorithm 3's tolerance: 1e-10                         */
+  int max_step_retries;    /* cap of Algorithm 2's retry loop: 60                    */
+  int precision;           /* PDLP_FP64 (default) or PDLP_FP32_BULK                  */
+  int inputs_on_device;    /* 0 host arrays (default), 1 device arrays              */
+  void* cuda_stream;       /* cudaStream_t or NULL                                  */
+  int64_t trace_iters;     /* > 0: record the first trace_iters accepted iterations  */
+  double* trace_out;       /* host array [trace_iters * (PDLP_TRACE_HEADER + n + m)] */
+  int profile;             /* 1: time the hot kernels with CUDA events (stats)       */
+  int verbose;             /* 1: one line per check to stderr                        */
+} pdlp_params;
+
+/* Trace record of one accepted iteration k (scaled space, i.e. of the
+ * preconditioned LP): PDLP_TRACE_HEADER doubles, then x[n], then y[m].
+ * header: [0] k, [1] accepted eta, [2] omega used, [3] eta_hat after,
+ *         [4] attempts in this iteration, [5] restart kind (0 none, 1 (i),
+ *         2 (ii), 3 (iii)), [6] mu(current), [7] mu(average) (NaN when not
+ *         evaluated at this iteration).                                           */
+#define PDLP_TRACE_HEADER 8
+
+typedef struct {
+  int status;
+  int64_t iterations;      /* accepted PDHG iterations                             */
+  int64_t attempts;        /* step attempts (accepted + rejected)                  */
+  int64_t rejected_steps;
+  int64_t restarts[3];     /* restarts by criterion (i), (ii), (iii)               */
+  double kkt_passes;       /* (number of A x products + number of A'y products)/2  */
+  double rel_kkt, rel_primal, rel_dual, rel_gap;
+  double primal_res_l2, dual_res_l2, primal_res_inf, dual_res_inf;
+  double pobj, dobj, paper_gap;
+  double omega, eta_hat;
+  double seconds_setup, seconds_solve, seconds_total;
+  /* profile == 1: device time of the two fused SpMV kernels and their launches */
+  double ms_spmv_a, ms_spmv_at, ms_primal, ms_checks;
+  int64_t launches_spmv_a, launches_spmv_at;
+  int64_t kernel_launches; /* kernels of this library launched by the call         */
+  double bytes_spmv_a, bytes_spmv_at; /* algorithmic bytes per launch              */
+} pdlp_stats;
+
+/* Fills *p with the defaults listed above. */
+void pdlp_params_default(pdlp_params* p);
+
+/* Solves the LP with PDLP (Algorithm 1 after the preconditioning of Sec. 3, the
+ * adaptive step of Algorithm 2, the restart scheme of Sec. 3 and the primal weight
+ * update of Algorithm 3).
+ *   m >= 0 rows, n >= 1 columns; A->nnz >= 0.
+ *   c[n], lc[m], uc[m], lv[n], uv[n]: lc <= uc, lv <= uv, lv < +inf, uv > -inf,
+ *       no NaN.  c finite.
+ *   x_out[n], y_out[m]: the returned point (unscaled).  Written for status >= 0.
+ *   stats: may be NULL.
+ * Errors: PDLP_INVALID_ARGUMENT for malformed input (the message names the first
+ * offending index), PDLP_OUT_OF_MEMORY, PDLP_CUDA_ERROR. */
+int pdlp_solve(int64_t m, int64_t n, const pdlp_csr* A, const double* c, const double* lc,
+               const double* uc, const double* lv, const double* uv, const pdlp_params* p,
+               double* x_out, double* y_out, pdlp_stats* stats);
+
+/* The diagonal preconditioning alone (Sec. 3 "Diagonal Preconditioning":
+ * p->ruiz_iters Ruiz passes, then Pock-Chambolle with p->pc_alpha), on the GPU.
+ * Writes d1_out[m], d2_out[n] (A~ = D1 A D2) and, if scaled_val_out is not NULL,
+ * the values of A~ in the order of A->val.  Same memory conventions as pdlp_solve. */
+int pdlp_precondition(int64_t m, int64_t n, const pdlp_csr* A, const pdlp_params* p,
+                      double* d1_out, double* d2_out, double* scaled_val_out);
+
+/* The normalized duality gap mu(z, z_ref) = rho_r(z) with r = ||z - z_ref||_omega
+ * (Sec. 3 "Adaptive restarts") of the point z = (x, y) for the LP exactly as given
+ * (no preconditioning), computed by the same GPU kernels the solver uses.
+ * x, x_ref: [n]; y, y_ref: [m]; x must lie in [lv, uv] and y in the sign set Y.
+ * Writes *mu_out (host).  Same memory conventions as pdlp_solve for the arrays. */
+int pdlp_normalized_gap(int64_t m, int64_t n, const pdlp_csr* A, const double* c,
+                        const double* lc, const double* uc, const double* lv,
+                        const double* uv, const double* x, const double* y,
+                        const double* x_ref, const double* y_ref, double omega,
+                        const pdlp_params* p, double* mu_out);
+
+/* Optimality measures of a point (x, y) for the LP as given: residuals, objectives
+ * and gaps with the reduced costs r = proj_R(c - A'y) (Sec. 2), as used by the
+ * termination test.  out[11] (host) receives: rel_kkt, rel_primal, rel_dual,
+ * rel_gap, primal_res_l2, dual_res_l2, primal_res_inf, dual_res_inf, pobj, dobj,
+ * paper_gap (Eq. (8)). */
+int pdlp_kkt(int64_t m, int64_t n, const pdlp_csr* A, const double* c, const double* lc,
+             const double* uc, const double* lv, const double* uv, const double* x,
+             const double* y, const pdlp_params* p, double* out);
+
+/* Message for the last nonzero return of a call made by this thread. */
+const char* pdlp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PDLP_H_ */

@@ -1,0 +1,792 @@
+// Periodic-check kernels: optimality measures (termination test) and the
+// normalized duality gap of Sec. 3 ("Adaptive restarts"), plus restart helpers.
+//
+// Normalized duality gap.  For z = (x, y) and radius r,
+//   r * rho_r(z) = max { L(x,yh) - L(xh,y) : zh in X x Y, ||zh - z||_omega <= r }.
+// The objective is separable: -g_j (xh_j - x_j) with g = c - A'y for every column, and
+// h_i(yh_i) - h_i(y_i) with h_i(s) = (lc_i - (Ax)_i) s for s > 0, (uc_i - (Ax)_i) s for
+// s < 0 for every row.  With a multiplier on the ball, parametrised by s = 1/lambda,
+// every coordinate of the maximiser follows a path with at most three linear pieces
+// (moving, parked at a bound or at 0, moving again), and along the path
+//     ||zh(s) - z||_omega^2 = alpha(s) s^2 + gamma(s),   F(s) = beta(s) s + phi(s)
+// with alpha, gamma, beta, phi piecewise constant: they change only at the
+// coordinates' breakpoints.  The kernels find the piece where the squared distance
+// crosses r^2 and solve alpha s^2 + gamma = r^2 there exactly:
+//   pass 0    (FP64) r, the slope at s = 0+, the fully saturated limit
+//   passes 1-4 (FP32) squared distance at kGapQ points: a geometric scan from the
+//             lower bound r / slope, then three linear refinements of the bracket
+//   exact     (FP64) coefficients at the bracket's left end, squared distance at its
+//             right end (verifies the bracket), and the breakpoints inside it
+//   finish    (one CTA) sorts those breakpoints and walks the pieces to the root.
+// If the FP32 scan mislocates the bracket or leaves too many breakpoints in it, the
+// host repeats the scan in FP64.
+#include <algorithm>
+#include <vector>
+
+#include "gap.cuh"
+
+namespace pdlp {
+
+__device__ __forceinline__ int64_t gi() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int64_t gs() { return (int64_t)gridDim.x * blockDim.x; }
+
+// ---------------------------------------------------------------------------
+// KKT sums of a point of the preconditioned LP, evaluated on the unscaled LP:
+// x = D2 x~, y = D1 y~, A x = D1^-1 (A~ x~), A'y = D2^-1 (A~' y~).
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(kThreads)
+    k_kkt(PointRef<T> z, OrigVecs o, int64_t m, int64_t n, KktScratch ks) {
+  __shared__ double red[5 * kWarps];
+  double v[5] = {0, 0, 0, 0, 0};  // pres2, dres2, pobj, dobj_rows, dobj_cols
+  double mx[2] = {0, 0};
+  for (int64_t i = gi(); i < m; i += gs()) {
+    const double ax = (double)z.ax[i] * o.inv_d1[i];
+    const double y = (double)z.y[i] * o.d1[i];
+    const double pr = ax - fmin(fmax(ax, o.lc[i]), o.uc[i]);
+    v[0] += pr * pr;
+    mx[0] = fmax(mx[0], fabs(pr));
+    if (y > 0.0)
+      v[3] += o.lc[i] * y;
+    else if (y < 0.0)
+      v[3] += o.uc[i] * y;
+  }
+  for (int64_t j = gi(); j < n; j += gs()) {
+    const double x = (double)z.x[j] * o.d2[j];
+    const double aty = (double)z.aty[j] * o.inv_d2[j];
+    const double g = o.c[j] - aty;
+    const bool lf = isfinite(o.lv[j]), uf = isfinite(o.uv[j]);
+    double r = g;
+    if (lf && !uf) r = fmax(g, 0.0);
+    if (!lf && uf) r = fmin(g, 0.0);
+    if (!lf && !uf) r = 0.0;
+    const double dr = g - r;
+    v[1] += dr * dr;
+    mx[1] = fmax(mx[1], fabs(dr));
+    v[2] += o.c[j] * x;
+    if (r > 0.0)
+      v[4] += o.lv[j] * r;
+    else if (r < 0.0)
+      v[4] += o.uv[j] * r;
+  }
+  block_sum<5>(v, red);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  mx[0] = warp_max(mx[0]);
+  mx[1] = warp_max(mx[1]);
+  __shared__ double mred[2 * kWarps];
+  if (lane == 0) {
+    mred[warp] = mx[0];
+    mred[kWarps + warp] = mx[1];
+  }
+  __syncthreads();
+  const int G = gridDim.x;
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0;
+    for (int w = 0; w < kWarps; ++w) {
+      a = fmax(a, mred[w]);
+      b = fmax(b, mred[kWarps + w]);
+    }
+    for (int k = 0; k < 5; ++k) ks.part[k * G + blockIdx.x] = v[k];
+    ks.part[5 * G + blockIdx.x] = a;
+    ks.part[6 * G + blockIdx.x] = b;
+  }
+  if (!last_block_arrival(ks.counter)) return;
+  double tot[5];
+  for (int k = 0; k < 5; ++k) tot[k] = block_sum_array(ks.part + k * G, G, red);
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0;
+    for (int i = 0; i < G; ++i) {
+      a = fmax(a, ((volatile double*)ks.part)[5 * G + i]);
+      b = fmax(b, ((volatile double*)ks.part)[6 * G + i]);
+    }
+    KktSums r;
+    r.pres2 = tot[0];
+    r.dres2 = tot[1];
+    r.pobj = tot[2];
+    r.dobj_rows = tot[3];
+    r.dobj_cols = tot[4];
+    r.pres_max = a;
+    r.dres_max = b;
+    *ks.out = r;
+  }
+}
+
+template <class T>
+void launch_kkt(const PointRef<T>& z, const OrigVecs& o, int64_t m, int64_t n,
+                const KktScratch& ks, cudaStream_t s) {
+  k_kkt<T><<<ks.grid, kThreads, 0, s>>>(z, o, m, n, ks);
+  PDLP_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------------------
+// restart helpers
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void k_average(const T* Sx, const T* Sy, const T* SAx, const T* SATy, double inv_w,
+                          const T* lv, const T* uv, T* x, T* y, T* ax, T* aty, int64_t m,
+                          int64_t n) {
+  const T w = (T)inv_w;
+  for (int64_t j = gi(); j < n; j += gs()) {
+    const T v = Sx[j] * w;
+    x[j] = v < lv[j] ? lv[j] : (v > uv[j] ? uv[j] : v);
+    aty[j] = SATy[j] * w;
+  }
+  for (int64_t i = gi(); i < m; i += gs()) {
+    y[i] = Sy[i] * w;
+    ax[i] = SAx[i] * w;
+  }
+}
+
+template <class T>
+void launch_average(const T* Sx, const T* Sy, const T* SAx, const T* SATy, double inv_w,
+                    const T* lv, const T* uv, T* x, T* y, T* ax, T* aty, int64_t m, int64_t n,
+                    cudaStream_t s) {
+  const int64_t need = (std::max(m, n) + kThreads - 1) / kThreads;
+  const int g = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 8));
+  k_average<T><<<g, kThreads, 0, s>>>(Sx, Sy, SAx, SATy, inv_w, lv, uv, x, y, ax, aty, m, n);
+  PDLP_LAUNCH_CHECK();
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads)
+    k_dist2(const T* x, const T* x0, const T* y, const T* y0, int64_t m, int64_t n, double* part,
+            unsigned int* counter, double* out2) {
+  __shared__ double red[2 * kWarps];
+  double v[2] = {0, 0};
+  for (int64_t j = gi(); j < n; j += gs()) {
+    const double d = (double)x[j] - (double)x0[j];
+    v[0] += d * d;
+  }
+  for (int64_t i = gi(); i < m; i += gs()) {
+    const double d = (double)y[i] - (double)y0[i];
+    v[1] += d * d;
+  }
+  block_sum<2>(v, red);
+  const int G = gridDim.x;
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = v[0];
+    part[G + blockIdx.x] = v[1];
+  }
+  if (!last_block_arrival(counter)) return;
+  const double a = block_sum_array(part, G, red);
+  const double b = block_sum_array(part + G, G, red);
+  if (threadIdx.x == 0) {
+    out2[0] = a;
+    out2[1] = b;
+  }
+}
+
+template <class T>
+void launch_dist2(const T* x, const T* x0, const T* y, const T* y0, int64_t m, int64_t n,
+                  double* part, unsigned int* counter, double* out2, int grid, cudaStream_t s) {
+  k_dist2<T><<<grid, kThreads, 0, s>>>(x, x0, y, y0, m, n, part, counter, out2);
+  PDLP_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------------------
+// normalized duality gap
+// ---------------------------------------------------------------------------
+enum { kGapActive = 0, kGapDone = 1, kGapFailed = 2, kGapNeedMore = 3 };
+enum { kPlanGeo = 0, kPlanLin = 1 };
+
+struct GapCtx {
+  int state;
+  int plan;
+  int ncand;
+  int unb;
+  double omega, r2, r;
+  double slope2, dinf2, finf;
+  double s_base;       // geometric plan: points s_base * 2^q
+  double s_lb;         // lower bound r / slope
+  double s_lo, s_hi;   // current bracket (linear plan)
+  double alpha, gamma, beta, phi, d2lo, d2hi;
+  double mu;
+};
+
+size_t gap_ctx_bytes() { return sizeof(GapCtx); }
+
+// Path of one column: g = c - A'y; it moves toward lv (g > 0) or uv (g < 0) at rate
+// |g| / omega per unit s and parks after travelling `room`.
+struct XPath {
+  double g, ga, room;
+  bool moves;
+};
+__device__ __forceinline__ XPath x_path(double x, double c, double aty, double lv, double uv) {
+  XPath p;
+  p.g = c - aty;
+  p.ga = fabs(p.g);
+  p.moves = p.g != 0.0;
+  p.room = p.g > 0.0 ? x - lv : (p.g < 0.0 ? uv - x : 0.0);
+  return p;
+}
+
+// Path of one row (kind 0: fixed; 1: moves away forever with slope k1; 2: moves to 0
+// with slope k1 and parks; 3: moves to 0, parks, then moves on with slope k2).
+struct YPath {
+  double y, k1, k2;
+  int kind;
+};
+__device__ __forceinline__ YPath y_path(double y, double lc, double uc, double ax) {
+  YPath p;
+  p.y = y;
+  p.k1 = 0.0;
+  p.k2 = 0.0;
+  p.kind = 0;
+  const bool lf = isfinite(lc), uf = isfinite(uc);
+  const double a = lc - ax, b = uc - ax;
+  if (y > 0.0) {
+    if (a > 0.0) {
+      p.kind = 1;
+      p.k1 = a;
+    } else if (a < 0.0) {
+      p.k1 = a;
+      if (uf && b < 0.0) {
+        p.kind = 3;
+        p.k2 = b;
+      } else {
+        p.kind = 2;
+      }
+    }
+  } else if (y < 0.0) {
+    if (b < 0.0) {
+      p.kind = 1;
+      p.k1 = b;
+    } else if (b > 0.0) {
+      p.k1 = b;
+      if (lf && a > 0.0) {
+        p.kind = 3;
+        p.k2 = a;
+      } else {
+        p.kind = 2;
+      }
+    }
+  } else {
+    if (lf && a > 0.0) {
+      p.kind = 1;
+      p.k1 = a;
+    } else if (uf && b < 0.0) {
+      p.kind = 1;
+      p.k1 = b;
+    }
+  }
+  return p;
+}
+
+// Coefficients (alpha, gamma, beta, phi) of a column / row at s.
+__device__ __forceinline__ void x_coef(const XPath& p, double s, double om, double* c4) {
+  if (!p.moves) return;
+  if (s * p.ga < om * p.room) {
+    const double w = p.g * p.g / om;
+    c4[0] += w;
+    c4[2] += w;
+  } else {
+    c4[1] += om * p.room * p.room;
+    c4[3] += p.ga * p.room;
+  }
+}
+__device__ __forceinline__ int y_piece(const YPath& p, double s, double om) {
+  // 1 moving (first piece), 2 parked at 0, 3 moving again
+  if (p.kind == 1) return 1;
+  const double ay = fabs(p.y);
+  if (s * (om * fabs(p.k1)) < ay) return 1;
+  if (p.kind == 3 && s * (om * fabs(p.k2)) >= ay) return 3;
+  return 2;
+}
+__device__ __forceinline__ void y_coef(const YPath& p, double s, double om, double* c4) {
+  if (p.kind == 0) return;
+  const int pc = y_piece(p, s, om);
+  if (pc == 1) {
+    const double w = om * p.k1 * p.k1;
+    c4[0] += w;
+    c4[2] += w;
+  } else if (pc == 2) {
+    c4[1] += p.y * p.y / om;
+    c4[3] += -p.k1 * p.y;
+  } else {
+    const double w = om * p.k2 * p.k2;
+    c4[0] += w;
+    c4[2] += w;
+    c4[3] += (p.k2 - p.k1) * p.y;
+  }
+}
+
+template <class T>
+struct GapArgs {
+  PointRef<T> z;
+  const T* x_ref;
+  const T* y_ref;
+  ScaledVecs<T> p;
+  GapCtx* ctx;
+  double* part;
+  unsigned int* counter;
+  int64_t* cand;
+};
+
+// pass 0: r^2, slope^2 at 0+, saturated limits, unbounded count
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_gap_pass0(GapArgs<T> a, double omega) {
+  __shared__ double red[5 * kWarps];
+  double v[5] = {0, 0, 0, 0, 0};  // r2, slope2, dinf2, finf, unb
+  const double om = omega;
+  for (int64_t j = gi(); j < a.p.n; j += gs()) {
+    const double x = a.z.x[j];
+    const double dx = x - (double)a.x_ref[j];
+    v[0] += om * dx * dx;
+    const XPath q = x_path(x, a.p.c[j], a.z.aty[j], a.p.lv[j], a.p.uv[j]);
+    if (!q.moves) continue;
+    if (isinf(q.room)) {
+      v[4] += 1.0;
+      continue;
+    }
+    if (q.room > 0.0) v[1] += q.g * q.g / om;
+    v[2] += om * q.room * q.room;
+    v[3] += q.ga * q.room;
+  }
+  for (int64_t i = gi(); i < a.p.m; i += gs()) {
+    const double y = a.z.y[i];
+    const double dy = y - (double)a.y_ref[i];
+    v[0] += dy * dy / om;
+    const YPath q = y_path(y, a.p.lc[i], a.p.uc[i], a.z.ax[i]);
+    if (q.kind == 0) continue;
+    v[1] += om * q.k1 * q.k1;
+    if (q.kind == 1 || q.kind == 3) {
+      v[4] += 1.0;
+      continue;
+    }
+    v[2] += q.y * q.y / om;
+    v[3] += -q.k1 * q.y;
+  }
+  block_sum<5>(v, red);
+  const int G = gridDim.x;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 5; ++k) a.part[k * G + blockIdx.x] = v[k];
+  if (!last_block_arrival(a.counter)) return;
+  double t[5];
+  for (int k = 0; k < 5; ++k) t[k] = block_sum_array(a.part + k * G, G, red);
+  if (threadIdx.x != 0) return;
+  GapCtx* c = a.ctx;
+  c->omega = om;
+  c->r2 = t[0];
+  c->r = sqrt(t[0]);
+  c->slope2 = t[1];
+  c->dinf2 = t[2];
+  c->finf = t[3];
+  c->unb = (int)t[4];
+  c->ncand = 0;
+  c->plan = kPlanGeo;
+  if (c->r2 == 0.0) {
+    c->mu = 0.0;
+    c->state = kGapDone;
+  } else if (c->unb == 0 && c->dinf2 <= c->r2) {
+    c->mu = c->finf / c->r;
+    c->state = kGapDone;
+  } else if (!(c->slope2 > 0.0)) {
+    c->mu = 0.0;
+    c->state = kGapDone;
+  } else {
+    c->s_lb = c->r / sqrt(c->slope2);
+    c->s_base = c->s_lb;
+    c->state = kGapActive;
+  }
+}
+
+// squared distance at kGapQ points, accumulated in Acc
+template <class T, class Acc>
+__global__ void __launch_bounds__(kThreads) k_gap_scan(GapArgs<T> a, int plan, int widen) {
+  __shared__ double red[kGapQ * kWarps];
+  __shared__ double s_pts[kGapQ];
+  GapCtx* c = a.ctx;
+  if (c->state != kGapActive || c->plan != plan) return;
+  const double om = c->omega;
+  if (threadIdx.x < kGapQ) {
+    const int q = threadIdx.x;
+    s_pts[q] = (plan == kPlanGeo) ? ldexp(c->s_base, q)
+                                  : c->s_lo + (c->s_hi - c->s_lo) * (double)(q + 1) / (double)(kGapQ + 1);
+  }
+  __syncthreads();
+  Acc pts[kGapQ];
+#pragma unroll
+  for (int q = 0; q < kGapQ; ++q) pts[q] = (Acc)s_pts[q];
+  Acc acc[kGapQ];
+#pragma unroll
+  for (int q = 0; q < kGapQ; ++q) acc[q] = (Acc)0;
+  const Acc omA = (Acc)om, iomA = (Acc)(1.0 / om);
+  for (int64_t j = gi(); j < a.p.n; j += gs()) {
+    const Acc x = (Acc)a.z.x[j];
+    const Acc g = (Acc)a.p.c[j] - (Acc)a.z.aty[j];
+    if (g == (Acc)0) continue;
+    const Acc room = g > (Acc)0 ? x - (Acc)a.p.lv[j] : (Acc)a.p.uv[j] - x;
+    const Acc ga = g > (Acc)0 ? g : -g;
+    const Acc orm = omA * room;
+    const Acc sat = omA * room * room;
+#pragma unroll
+    for (int q = 0; q < kGapQ; ++q) {
+      const Acc t = pts[q] * ga;
+      acc[q] += (t < orm) ? t * t * iomA : sat;
+    }
+  }
+  for (int64_t i = gi(); i < a.p.m; i += gs()) {
+    const YPath q0 = y_path((double)a.z.y[i], (double)a.p.lc[i], (double)a.p.uc[i],
+                            (double)a.z.ax[i]);
+    if (q0.kind == 0) continue;
+    const Acc w1 = omA * (Acc)fabs(q0.k1), w2 = omA * (Acc)fabs(q0.k2);
+    const Acc ay = (Acc)fabs(q0.y), y2 = (Acc)(q0.y * q0.y) * iomA;
+    const int kind = q0.kind;
+#pragma unroll
+    for (int q = 0; q < kGapQ; ++q) {
+      const Acc t1 = pts[q] * w1;
+      Acc v;
+      if (kind == 1 || t1 < ay) {
+        v = t1 * t1 * iomA;
+      } else {
+        const Acc t2 = pts[q] * w2;
+        v = (kind == 3 && t2 >= ay) ? t2 * t2 * iomA : y2;
+      }
+      acc[q] += v;
+    }
+  }
+  double v[kGapQ];
+#pragma unroll
+  for (int q = 0; q < kGapQ; ++q) v[q] = (double)acc[q];
+  block_sum<kGapQ>(v, red);
+  const int G = gridDim.x;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < kGapQ; ++q) a.part[q * G + blockIdx.x] = v[q];
+  if (!last_block_arrival(a.counter)) return;
+  __shared__ double d2[kGapQ];
+  for (int q = 0; q < kGapQ; ++q) {
+    const double t = block_sum_array(a.part + q * G, G, red);
+    if (threadIdx.x == 0) d2[q] = t;
+  }
+  if (threadIdx.x != 0) return;
+  int first = -1;
+  for (int q = 0; q < kGapQ; ++q)
+    if (d2[q] >= c->r2) {
+      first = q;
+      break;
+    }
+  if (plan == kPlanGeo) {
+    if (first < 0) {
+      c->state = kGapNeedMore;
+      return;
+    }
+    c->s_lo = first == 0 ? 0.5 * s_pts[0] : s_pts[first - 1];
+    c->s_hi = s_pts[first];
+    c->plan = kPlanLin;
+  } else {
+    int lo_i = (first < 0 ? kGapQ : first) - 1;  // bracket [p_lo_i, p_lo_i+1], p_-1 = s_lo
+    int hi_i = lo_i + 1;
+    if (widen) {
+      lo_i -= 1;
+      hi_i += 1;
+    }
+    const double nlo = lo_i < 0 ? c->s_lo : s_pts[lo_i];
+    const double nhi = hi_i >= kGapQ ? c->s_hi : s_pts[hi_i];
+    c->s_lo = nlo;
+    c->s_hi = nhi;
+  }
+}
+
+// exact FP64 coefficients at s_lo, squared distance at s_hi, breakpoints in (s_lo, s_hi]
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_gap_exact(GapArgs<T> a) {
+  __shared__ double red[5 * kWarps];
+  GapCtx* c = a.ctx;
+  if (c->state != kGapActive) return;
+  const double om = c->omega, slo = c->s_lo, shi = c->s_hi;
+  double v[5] = {0, 0, 0, 0, 0};  // alpha, gamma, beta, phi at s_lo; d2 at s_hi
+  for (int64_t j = gi(); j < a.p.n; j += gs()) {
+    const XPath q = x_path(a.z.x[j], a.p.c[j], a.z.aty[j], a.p.lv[j], a.p.uv[j]);
+    if (!q.moves) continue;
+    x_coef(q, slo, om, v);
+    double h[4] = {0, 0, 0, 0};
+    x_coef(q, shi, om, h);
+    v[4] += h[0] * shi * shi + h[1];
+    const double orm = om * q.room;
+    if (slo * q.ga < orm && orm <= shi * q.ga) {
+      const int k = atomicAdd(&c->ncand, 1);
+      if (k < kGapCandCap) a.cand[k] = j * 4 + 0;
+    }
+  }
+  for (int64_t i = gi(); i < a.p.m; i += gs()) {
+    const YPath q = y_path(a.z.y[i], a.p.lc[i], a.p.uc[i], a.z.ax[i]);
+    if (q.kind == 0) continue;
+    y_coef(q, slo, om, v);
+    double h[4] = {0, 0, 0, 0};
+    y_coef(q, shi, om, h);
+    v[4] += h[0] * shi * shi + h[1];
+    if (q.kind == 1) continue;
+    const double ay = fabs(q.y);
+    const double w1 = om * fabs(q.k1);
+    if (slo * w1 < ay && ay <= shi * w1) {
+      const int k = atomicAdd(&c->ncand, 1);
+      if (k < kGapCandCap) a.cand[k] = i * 4 + 1;
+    }
+    if (q.kind == 3) {
+      const double w2 = om * fabs(q.k2);
+      if (slo * w2 < ay && ay <= shi * w2) {
+        const int k = atomicAdd(&c->ncand, 1);
+        if (k < kGapCandCap) a.cand[k] = i * 4 + 2;
+      }
+    }
+  }
+  block_sum<5>(v, red);
+  const int G = gridDim.x;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 5; ++k) a.part[k * G + blockIdx.x] = v[k];
+  if (!last_block_arrival(a.counter)) return;
+  double t[5];
+  for (int k = 0; k < 5; ++k) t[k] = block_sum_array(a.part + k * G, G, red);
+  if (threadIdx.x != 0) return;
+  c->alpha = t[0];
+  c->gamma = t[1];
+  c->beta = t[2];
+  c->phi = t[3];
+  c->d2lo = t[0] * slo * slo + t[1];
+  c->d2hi = t[4];
+  const int nc = ((volatile int*)&c->ncand)[0];
+  if (!(c->d2lo < c->r2 && c->d2hi >= c->r2) || nc > kGapCandCap) c->state = kGapFailed;
+}
+
+// breakpoint value and coefficient change of one candidate
+template <class T>
+__device__ void cand_info(const GapArgs<T>& a, double om, int64_t code, double* bp, double* d4) {
+  const int64_t idx = code >> 2;
+  const int which = (int)(code & 3);
+  d4[0] = d4[1] = d4[2] = d4[3] = 0.0;
+  if (which == 0) {
+    const XPath q = x_path(a.z.x[idx], a.p.c[idx], a.z.aty[idx], a.p.lv[idx], a.p.uv[idx]);
+    *bp = om * q.room / q.ga;
+    const double w = q.g * q.g / om;
+    d4[0] = -w;
+    d4[1] = om * q.room * q.room;
+    d4[2] = -w;
+    d4[3] = q.ga * q.room;
+  } else {
+    const YPath q = y_path(a.z.y[idx], a.p.lc[idx], a.p.uc[idx], a.z.ax[idx]);
+    const double ay = fabs(q.y);
+    if (which == 1) {
+      *bp = ay / (om * fabs(q.k1));
+      const double w = om * q.k1 * q.k1;
+      d4[0] = -w;
+      d4[1] = q.y * q.y / om;
+      d4[2] = -w;
+      d4[3] = -q.k1 * q.y;
+    } else {
+      *bp = ay / (om * fabs(q.k2));
+      const double w = om * q.k2 * q.k2;
+      d4[0] = w;
+      d4[1] = -q.y * q.y / om;
+      d4[2] = w;
+      d4[3] = q.k2 * q.y;
+    }
+  }
+}
+
+constexpr int kFinPer = kGapCandCap / kThreads;
+
+// one CTA: sort the breakpoints, prefix-sum their coefficient changes, find the piece
+// where alpha s^2 + gamma reaches r^2 and solve there
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_gap_finish(GapArgs<T> a) {
+  __shared__ double s_key[kGapCandCap];
+  __shared__ long long s_code[kGapCandCap];
+  __shared__ double s_wsum[4][kWarps];
+  __shared__ int s_first;
+  GapCtx* c = a.ctx;
+  if (c->state != kGapActive) return;
+  const double om = c->omega;
+  const int nc = c->ncand;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < kGapCandCap; i += kThreads) {
+    if (i < nc) {
+      double d4[4];
+      double bp;
+      cand_info(a, om, a.cand[i], &bp, d4);
+      s_key[i] = bp;
+      s_code[i] = a.cand[i];
+    } else {
+      s_key[i] = INFINITY;
+      s_code[i] = LLONG_MAX;
+    }
+  }
+  __syncthreads();
+  // bitonic sort by (key, code)
+  for (int k = 2; k <= kGapCandCap; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < kGapCandCap; i += kThreads) {
+        const int l = i ^ j;
+        if (l > i) {
+          const bool up = (i & k) == 0;
+          const double ki = s_key[i], kl = s_key[l];
+          const long long ci = s_code[i], cl = s_code[l];
+          const bool gt = (ki > kl) || (ki == kl && ci > cl);
+          if (gt == up) {
+            s_key[i] = kl;
+            s_key[l] = ki;
+            s_code[i] = cl;
+            s_code[l] = ci;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // exclusive prefix of the coefficient changes in sorted order; thread t owns the
+  // consecutive items [t*kFinPer, (t+1)*kFinPer)
+  double dl[kFinPer][4];
+  double run[4] = {0, 0, 0, 0};
+  for (int q = 0; q < kFinPer; ++q) {
+    const int i = tid * kFinPer + q;
+    double d4[4] = {0, 0, 0, 0};
+    if (i < nc) {
+      double bp;
+      cand_info(a, om, s_code[i], &bp, d4);
+    }
+    for (int k = 0; k < 4; ++k) {
+      dl[q][k] = run[k];
+      run[k] += d4[k];
+    }
+  }
+  const int lane = tid & 31, warp = tid >> 5;
+  double off[4];
+  for (int k = 0; k < 4; ++k) {
+    double inc = run[k];
+    for (int o = 1; o < 32; o <<= 1) {
+      const double t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    if (lane == 31) s_wsum[k][warp] = inc;
+    off[k] = inc - run[k];
+  }
+  if (tid == 0) s_first = INT_MAX;
+  __syncthreads();
+  for (int k = 0; k < 4; ++k)
+    for (int w = 0; w < warp; ++w) off[k] += s_wsum[k][w];
+  const double al0 = c->alpha, ga0 = c->gamma, r2 = c->r2;
+  for (int q = 0; q < kFinPer; ++q) {
+    const int i = tid * kFinPer + q;
+    if (i >= nc) break;
+    const double al = al0 + (off[0] + dl[q][0]);
+    const double gm = ga0 + (off[1] + dl[q][1]);
+    const double b = s_key[i];
+    if (al * b * b + gm >= r2) {
+      atomicMin(&s_first, i);
+      break;
+    }
+  }
+  __syncthreads();
+  const int first = s_first;
+  // coefficients of the crossing piece: exclusive prefix at `first` (or the total)
+  const int owner = (first == INT_MAX) ? -1 : first / kFinPer;
+  __shared__ double s_coef[4];
+  __shared__ double s_tot[4];
+  if (tid == kThreads - 1)
+    for (int k = 0; k < 4; ++k) s_tot[k] = off[k] + run[k];
+  if (tid == owner)
+    for (int k = 0; k < 4; ++k) s_coef[k] = off[k] + dl[first - owner * kFinPer][k];
+  __syncthreads();
+  if (tid != 0) return;
+  double cf[4];
+  double lo_b, hi_b;
+  if (first == INT_MAX) {
+    for (int k = 0; k < 4; ++k) cf[k] = s_tot[k];
+    lo_b = nc > 0 ? s_key[nc - 1] : c->s_lo;
+    hi_b = c->s_hi;
+  } else {
+    for (int k = 0; k < 4; ++k) cf[k] = s_coef[k];
+    lo_b = first == 0 ? c->s_lo : s_key[first - 1];
+    hi_b = s_key[first];
+  }
+  const double al = c->alpha + cf[0], gm = c->gamma + cf[1];
+  const double be = c->beta + cf[2], ph = c->phi + cf[3];
+  double s_star = lo_b;
+  if (al > 0.0) s_star = sqrt(fmax(r2 - gm, 0.0) / al);
+  s_star = fmin(fmax(s_star, lo_b), hi_b);
+  c->mu = (be * s_star + ph) / c->r;
+  c->state = kGapDone;
+}
+
+__global__ void k_gap_set(GapCtx* c, int state, int plan, double base_scale) {
+  c->state = state;
+  c->plan = plan;
+  if (plan == kPlanGeo) c->s_base = c->s_lb * base_scale;
+  c->ncand = 0;
+}
+__global__ void k_gap_clear_cand(GapCtx* c) { c->ncand = 0; }
+
+template <class T>
+double normalized_gap(const PointRef<T>& z, const T* x_ref, const T* y_ref, double omega,
+                      const ScaledVecs<T>& p, const GapScratch& gsc, cudaStream_t s,
+                      int* launches) {
+  GapArgs<T> a;
+  a.z = z;
+  a.x_ref = x_ref;
+  a.y_ref = y_ref;
+  a.p = p;
+  a.ctx = gsc.ctx;
+  a.part = gsc.part;
+  a.counter = gsc.counter;
+  a.cand = gsc.cand;
+  const int G = gsc.grid;
+  int nl = 0;
+  k_gap_pass0<T><<<G, kThreads, 0, s>>>(a, omega);
+  k_gap_scan<T, float><<<G, kThreads, 0, s>>>(a, kPlanGeo, 0);
+  k_gap_scan<T, float><<<G, kThreads, 0, s>>>(a, kPlanLin, 0);
+  k_gap_scan<T, float><<<G, kThreads, 0, s>>>(a, kPlanLin, 0);
+  k_gap_scan<T, float><<<G, kThreads, 0, s>>>(a, kPlanLin, 1);
+  k_gap_exact<T><<<G, kThreads, 0, s>>>(a);
+  k_gap_finish<T><<<1, kThreads, 0, s>>>(a);
+  nl += 7;
+  PDLP_LAUNCH_CHECK();
+  GapCtx h;
+  PDLP_CUDA_CHECK(cudaMemcpyAsync(&h, gsc.ctx, sizeof(GapCtx), cudaMemcpyDeviceToHost, s));
+  PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+  if (h.state != kGapDone) {
+    // FP64 scan from the lower bound, octave block by octave block
+    double scale = 1.0;
+    for (int rep = 0; rep < 64; ++rep) {
+      k_gap_set<<<1, 1, 0, s>>>(gsc.ctx, kGapActive, kPlanGeo, scale);
+      k_gap_scan<T, double><<<G, kThreads, 0, s>>>(a, kPlanGeo, 0);
+      nl += 2;
+      PDLP_LAUNCH_CHECK();
+      PDLP_CUDA_CHECK(cudaMemcpyAsync(&h, gsc.ctx, sizeof(GapCtx), cudaMemcpyDeviceToHost, s));
+      PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+      if (h.state != kGapNeedMore) break;
+      scale = ldexp(scale, kGapQ);
+    }
+    if (h.state != kGapActive) throw PdlpError(5, "normalized duality gap: no bracket found");
+    for (int rep = 0; rep < 80; ++rep) {
+      k_gap_clear_cand<<<1, 1, 0, s>>>(gsc.ctx);
+      k_gap_exact<T><<<G, kThreads, 0, s>>>(a);
+      k_gap_finish<T><<<1, kThreads, 0, s>>>(a);
+      nl += 3;
+      PDLP_LAUNCH_CHECK();
+      PDLP_CUDA_CHECK(cudaMemcpyAsync(&h, gsc.ctx, sizeof(GapCtx), cudaMemcpyDeviceToHost, s));
+      PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+      if (h.state == kGapDone) break;
+      k_gap_set<<<1, 1, 0, s>>>(gsc.ctx, kGapActive, kPlanLin, 1.0);
+      k_gap_scan<T, double><<<G, kThreads, 0, s>>>(a, kPlanLin, 0);
+      nl += 2;
+      PDLP_LAUNCH_CHECK();
+    }
+    if (h.state != kGapDone) throw PdlpError(5, "normalized duality gap: bracket refinement failed");
+  }
+  if (launches) *launches += nl;
+  return h.mu;
+}
+
+#define PDLP_GAP_INST(T)                                                                       \
+  template void launch_kkt<T>(const PointRef<T>&, const OrigVecs&, int64_t, int64_t,            \
+                              const KktScratch&, cudaStream_t);                                 \
+  template double normalized_gap<T>(const PointRef<T>&, const T*, const T*, double,             \
+                                    const ScaledVecs<T>&, const GapScratch&, cudaStream_t,      \
+                                    int*);                                                      \
+  template void launch_average<T>(const T*, const T*, const T*, const T*, double, const T*,     \
+                                  const T*, T*, T*, T*, T*, int64_t, int64_t, cudaStream_t);    \
+  template void launch_dist2<T>(const T*, const T*, const T*, const T*, int64_t, int64_t,       \
+                                double*, unsigned int*, double*, int, cudaStream_t);
+PDLP_GAP_INST(double)
+PDLP_GAP_INST(float)
+
+}  // namespace pdlp

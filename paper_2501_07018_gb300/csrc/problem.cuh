@@ -1,0 +1,116 @@
+// Device-resident problem layout and the launcher interface between the host driver
+// (solver.cu) and the kernel translation units (setup.cu, pdhg.cu, gap.cu).
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace pdlp {
+
+// Row tiling of a CSR matrix for the fused SpMV kernels.
+//   A "tile" is the set of rows whose merge-path coordinate r + row_ptr[r] falls in
+//   [t*kTileDiag, (t+1)*kTileDiag): at most kTileDiag rows and, excluding a long
+//   last row, fewer than kTileDiag + kLongRow nonzeros, so it fits the kChunk-entry
+//   shared-memory stage.  A row with more than kLongRow nonzeros is a "long row":
+//   it is always the last row of its tile, the tile skips it, and it is processed
+//   in kChunk-sized chunks by separate work items whose partial sums are combined,
+//   in chunk order, by the last chunk to finish.
+constexpr int kTileDiag = 1024;
+constexpr int kLongRow = 1024;
+constexpr int kChunk = 2048;
+static_assert(kTileDiag + kLongRow <= kChunk, "tile stage too small");
+
+template <class T>
+struct Mat {
+  int64_t rows = 0, cols = 0, nnz = 0;
+  int64_t* row_ptr = nullptr;  // [rows+1]
+  int32_t* col = nullptr;      // [nnz]
+  T* val = nullptr;            // [nnz]
+  int32_t ntiles = 0;
+  int32_t* tile_row = nullptr;     // [ntiles+1] first row of each tile
+  int32_t nlong = 0;
+  int32_t* long_rows = nullptr;    // [nlong]
+  int64_t nchunks = 0;
+  int64_t* chunk_ptr = nullptr;    // [nlong+1] first chunk of each long row
+  int32_t* chunk_owner = nullptr;  // [nchunks] long-row index of each chunk
+  unsigned int* long_cnt = nullptr;  // [nlong] arrival counters (kept at 0 between launches)
+  double* long_part = nullptr;       // [nchunks] chunk partial sums
+  double* long_contrib = nullptr;    // [nlong * 2] per-long-row reduction contributions
+  int64_t work_items() const { return (int64_t)ntiles + nchunks; }
+};
+
+// Simple owning list of device allocations, freed together.
+class DeviceArena {
+ public:
+  ~DeviceArena() { release(); }
+  void* alloc_bytes(size_t bytes) {
+    void* p = nullptr;
+    if (bytes == 0) bytes = 16;
+    PDLP_CUDA_CHECK(cudaMalloc(&p, (bytes + 255) & ~size_t(255)));
+    ptrs_.push_back(p);
+    total_ += bytes;
+    return p;
+  }
+  template <class U>
+  U* alloc(int64_t count) {
+    return static_cast<U*>(alloc_bytes(sizeof(U) * (size_t)(count > 0 ? count : 1)));
+  }
+  void release() {
+    for (void* p : ptrs_) cudaFree(p);
+    ptrs_.clear();
+  }
+  size_t total() const { return total_; }
+
+ private:
+  std::vector<void*> ptrs_;
+  size_t total_ = 0;
+};
+
+// Number of CTAs of the persistent / grid-stride kernels on this device.
+int grid_ctas(int per_sm);
+int num_sms();
+
+// ---------------------------------------------------------------------------
+// setup.cu
+// ---------------------------------------------------------------------------
+struct ValidateFlags {
+  unsigned long long bad_rowptr, bad_col, bad_val, bad_c, bad_rows, bad_cols;
+};
+void validate_rowptr(const int64_t* row_ptr, int64_t m, int64_t nnz, ValidateFlags* flags,
+                     cudaStream_t s);
+void validate_entries(const int64_t* row_ptr, const int32_t* col, const double* val, int64_t m,
+                      int64_t n, ValidateFlags* flags, cudaStream_t s);
+void validate_vectors(const double* c, const double* lc, const double* uc, const double* lv,
+                      const double* uv, int64_t m, int64_t n, ValidateFlags* flags,
+                      cudaStream_t s);
+
+// CSR transpose by a stable LSD radix sort of the column indices: within each row of
+// the transpose, entries keep increasing original-row order.
+void transpose_csr(DeviceArena& arena, const int64_t* row_ptr, const int32_t* col,
+                   const double* val, int64_t m, int64_t n, int64_t nnz, int64_t* t_row_ptr,
+                   int32_t* t_col, double* t_val, cudaStream_t s);
+
+// kind: 0 = max |a| over the row, 1 = sum |a|, 2 = (sum |a|^p)^(1/p)
+void row_norms(const int64_t* row_ptr, const double* val, int64_t rows, int kind, double p,
+               double* out, cudaStream_t s);
+// out_i = (v_i > 0) ? 1/sqrt(v_i) : 1 ;  acc_i *= out_i
+void scale_factors(const double* norms, int64_t len, double* factors, double* acc,
+                   cudaStream_t s);
+// val_e <- (val_e * f_col[col_e]) * f_row[row]   when col_first (A-side: f_col = row
+// factor of A applied first ...).  See setup.cu for the exact operand order.
+void scale_values(const int64_t* row_ptr, const int32_t* col, double* val, int64_t rows,
+                  const double* f_first, const double* f_second, bool first_is_col,
+                  cudaStream_t s);
+double max_abs(DeviceArena& arena, const double* v, int64_t len, cudaStream_t s);
+
+template <class T>
+void build_tiles(DeviceArena& arena, Mat<T>& M, cudaStream_t s);
+template <class T>
+void convert_values(const double* src, T* dst, int64_t len, cudaStream_t s);
+
+// exclusive scan of int64 values (in place allowed); out[len] receives the total
+void exclusive_scan_i64(DeviceArena& arena, const int64_t* in, int64_t* out, int64_t len,
+                        cudaStream_t s);
+
+}  // namespace pdlp

@@ -1,0 +1,1075 @@
+// Host driver of the library: the C ABI of include/pdlp.h.
+//
+// pdlp_solve runs Algorithm 1 of the paper after the preconditioning of Sec. 3.  The
+// step attempts run on the device without host round trips: each attempt is three
+// kernel launches (primal step; A x' with the dual step and Algorithm 2's accept
+// test; A'y' with the running averages), and the device-side state decides whether
+// the attempt became the new iterate.  The host only synchronises at the iteration
+// counts where something else happens -- every check_period accepted iterations
+// (termination and restart evaluation), and whenever restart condition (iii) can fire
+// -- which it computes in advance from (k, t).
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "../../include/pdlp.h"
+#include "gap.cuh"
+#include "pdhg.cuh"
+
+namespace pdlp {
+
+static thread_local std::string g_last_error;
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+__device__ __forceinline__ int64_t sgi() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int64_t sgs() { return (int64_t)gridDim.x * blockDim.x; }
+
+static unsigned vec_grid(int64_t len) {
+  const int64_t need = (len + kThreads - 1) / kThreads;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 8));
+}
+
+// ---------------------------------------------------------------------------
+// small vector kernels of the driver
+// ---------------------------------------------------------------------------
+// Preconditioned vectors (Sec. 3): c~ = D2 c, (lc~, uc~) = D1 (lc, uc), (lv~, uv~) = D2^-1 (lv, uv)
+template <class T>
+__global__ void k_scale_vectors(const double* c, const double* lc, const double* uc,
+                                const double* lv, const double* uv, const double* d1,
+                                const double* d2, int64_t m, int64_t n, T* sc, T* slc, T* suc,
+                                T* slv, T* suv, double* inv_d1, double* inv_d2) {
+  for (int64_t j = sgi(); j < n; j += sgs()) {
+    sc[j] = (T)(d2[j] * c[j]);
+    slv[j] = (T)(lv[j] / d2[j]);
+    suv[j] = (T)(uv[j] / d2[j]);
+    inv_d2[j] = 1.0 / d2[j];
+  }
+  for (int64_t i = sgi(); i < m; i += sgs()) {
+    slc[i] = (T)(d1[i] * lc[i]);
+    suc[i] = (T)(d1[i] * uc[i]);
+    inv_d1[i] = 1.0 / d1[i];
+  }
+}
+
+// sum of squares of c and of Combine(lc, uc) (Sec. 3, "Initialization of the primal
+// weights"), deterministic: per-CTA partials, fixed-order final sum
+template <class T>
+__global__ void __launch_bounds__(kThreads)
+    k_norms(const T* c, const T* lc, const T* uc, int64_t m, int64_t n, double* part,
+            unsigned int* counter, double* out) {
+  __shared__ double red[2 * kWarps];
+  double v[2] = {0, 0};
+  for (int64_t j = sgi(); j < n; j += sgs()) {
+    const double x = c[j];
+    v[0] += x * x;
+  }
+  for (int64_t i = sgi(); i < m; i += sgs()) {
+    const double l = lc[i], u = uc[i];
+    const double lf = isfinite(l) ? fabs(l) : 0.0, uf = isfinite(u) ? fabs(u) : 0.0;
+    const double b = fmax(0.0, fmax(lf, uf));
+    v[1] += b * b;
+  }
+  block_sum<2>(v, red);
+  const int G = gridDim.x;
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = v[0];
+    part[G + blockIdx.x] = v[1];
+  }
+  if (!last_block_arrival(counter)) return;
+  const double a = block_sum_array(part, G, red);
+  const double b = block_sum_array(part + G, G, red);
+  if (threadIdx.x == 0) {
+    out[0] = a;
+    out[1] = b;
+  }
+}
+
+template <class T>
+__global__ void k_init_point(const T* lv, const T* uv, T* x, T* y, T* aty, T* x0, T* y0,
+                             int64_t m, int64_t n) {
+  for (int64_t j = sgi(); j < n; j += sgs()) {
+    const T lo = lv[j], hi = uv[j];
+    const T v = (T)0 < lo ? lo : ((T)0 > hi ? hi : (T)0);  // proj_X(0)
+    x[j] = v;
+    x0[j] = v;
+    aty[j] = (T)0;
+  }
+  for (int64_t i = sgi(); i < m; i += sgs()) {
+    y[i] = (T)0;
+    y0[i] = (T)0;
+  }
+}
+
+template <class T>
+__global__ void k_set_point(const double* xs, const double* ys, T* x, T* y, T* x0, T* y0,
+                            int64_t m, int64_t n) {
+  for (int64_t j = sgi(); j < n; j += sgs()) {
+    x[j] = (T)xs[j];
+    x0[j] = (T)xs[j];
+  }
+  for (int64_t i = sgi(); i < m; i += sgs()) {
+    y[i] = (T)ys[i];
+    y0[i] = (T)ys[i];
+  }
+}
+
+template <class T>
+__global__ void k_copy2(const T* a, T* a_out, int64_t na, const T* b, T* b_out, int64_t nb) {
+  for (int64_t j = sgi(); j < na; j += sgs()) a_out[j] = a[j];
+  for (int64_t i = sgi(); i < nb; i += sgs()) b_out[i] = b[i];
+}
+
+template <class T>
+__global__ void k_unscale(const T* x, const T* y, const double* d1, const double* d2, double* xo,
+                          double* yo, int64_t m, int64_t n) {
+  for (int64_t j = sgi(); j < n; j += sgs()) xo[j] = d2[j] * (double)x[j];
+  for (int64_t i = sgi(); i < m; i += sgs()) yo[i] = d1[i] * (double)y[i];
+}
+
+template <class T>
+__global__ void k_to_double2(const T* x, double* xo, int64_t n, const T* y, double* yo, int64_t m) {
+  for (int64_t j = sgi(); j < n; j += sgs()) xo[j] = (double)x[j];
+  for (int64_t i = sgi(); i < m; i += sgs()) yo[i] = (double)y[i];
+}
+
+__global__ void k_fill(double* v, int64_t n, double val) {
+  for (int64_t i = sgi(); i < n; i += sgs()) v[i] = val;
+}
+
+// ---------------------------------------------------------------------------
+// inputs
+// ---------------------------------------------------------------------------
+struct Inputs {
+  int64_t m, n, nnz;
+  const int64_t* row_ptr;
+  const int32_t* col;
+  const double* val;
+  const double *c, *lc, *uc, *lv, *uv;
+  bool on_device;
+};
+
+struct DevInputs {
+  int64_t* row_ptr;
+  int32_t* col;
+  double* val;  // modifiable copy (scaled in place)
+  double *c, *lc, *uc, *lv, *uv;
+};
+
+static void copy_in(void* dst, const void* src, size_t bytes, bool on_device, cudaStream_t s) {
+  if (bytes == 0) return;
+  PDLP_CUDA_CHECK(cudaMemcpyAsync(dst, src, bytes,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+}
+
+static void check_args(const Inputs& in) {
+  if (in.m < 0 || in.n < 1) throw PdlpError(-1, "need m >= 0 and n >= 1");
+  if (in.n > INT32_MAX || in.m > INT32_MAX - 1)
+    throw PdlpError(-1, "m and n must fit 32-bit indices");
+  if (in.nnz < 0) throw PdlpError(-1, "nnz < 0");
+  if (!in.row_ptr || (in.nnz > 0 && (!in.col || !in.val)))
+    throw PdlpError(-1, "null matrix array");
+  if (!in.c || !in.lv || !in.uv || (in.m > 0 && (!in.lc || !in.uc)))
+    throw PdlpError(-1, "null vector argument");
+}
+
+static DevInputs stage_inputs(DeviceArena& arena, const Inputs& in, cudaStream_t s) {
+  DevInputs d;
+  d.row_ptr = arena.alloc<int64_t>(in.m + 1);
+  d.col = arena.alloc<int32_t>(in.nnz);
+  d.val = arena.alloc<double>(in.nnz);
+  d.c = arena.alloc<double>(in.n);
+  d.lv = arena.alloc<double>(in.n);
+  d.uv = arena.alloc<double>(in.n);
+  d.lc = arena.alloc<double>(in.m);
+  d.uc = arena.alloc<double>(in.m);
+  copy_in(d.row_ptr, in.row_ptr, sizeof(int64_t) * (in.m + 1), in.on_device, s);
+  copy_in(d.col, in.col, sizeof(int32_t) * in.nnz, in.on_device, s);
+  copy_in(d.val, in.val, sizeof(double) * in.nnz, in.on_device, s);
+  copy_in(d.c, in.c, sizeof(double) * in.n, in.on_device, s);
+  copy_in(d.lv, in.lv, sizeof(double) * in.n, in.on_device, s);
+  copy_in(d.uv, in.uv, sizeof(double) * in.n, in.on_device, s);
+  copy_in(d.lc, in.lc, sizeof(double) * in.m, in.on_device, s);
+  copy_in(d.uc, in.uc, sizeof(double) * in.m, in.on_device, s);
+  return d;
+}
+
+static void validate(DeviceArena& arena, const Inputs& in, const DevInputs& d, cudaStream_t s) {
+  ValidateFlags* f = arena.alloc<ValidateFlags>(1);
+  PDLP_CUDA_CHECK(cudaMemsetAsync(f, 0xff, sizeof(ValidateFlags), s));
+  validate_rowptr(d.row_ptr, in.m, in.nnz, f, s);
+  ValidateFlags h;
+  PDLP_CUDA_CHECK(cudaMemcpyAsync(&h, f, sizeof(h), cudaMemcpyDeviceToHost, s));
+  PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+  const unsigned long long none = ~0ull;
+  if (h.bad_rowptr != none)
+    throw PdlpError(-1, "row_ptr invalid at index " + std::to_string(h.bad_rowptr) +
+                            " (need row_ptr[0]=0, nondecreasing, row_ptr[m]=nnz)");
+  validate_entries(d.row_ptr, d.col, d.val, in.m, in.n, f, s);
+  validate_vectors(d.c, d.lc, d.uc, d.lv, d.uv, in.m, in.n, f, s);
+  PDLP_CUDA_CHECK(cudaMemcpyAsync(&h, f, sizeof(h), cudaMemcpyDeviceToHost, s));
+  PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+  if (h.bad_col != none)
+    throw PdlpError(-1, "column indices of row " + std::to_string(h.bad_col) +
+                            " out of range or not strictly increasing");
+  if (h.bad_val != none)
+    throw PdlpError(-1, "non-finite matrix value at position " + std::to_string(h.bad_val));
+  if (h.bad_c != none) throw PdlpError(-1, "non-finite c at index " + std::to_string(h.bad_c));
+  if (h.bad_cols != none)
+    throw PdlpError(-1, "variable bounds invalid at index " + std::to_string(h.bad_cols) +
+                            " (NaN, lv > uv, lv = +inf or uv = -inf)");
+  if (h.bad_rows != none)
+    throw PdlpError(-1, "row bounds invalid at index " + std::to_string(h.bad_rows) +
+                            " (NaN, lc > uc, lc = +inf or uc = -inf)");
+}
+
+// ---------------------------------------------------------------------------
+// preconditioned problem
+// ---------------------------------------------------------------------------
+template <class T>
+struct Problem {
+  int64_t m = 0, n = 0, nnz = 0;
+  Mat<T> A, AT;
+  double* val64 = nullptr;   // A~ values in FP64
+  double* valT64 = nullptr;  // A~' values in FP64
+  double *d1 = nullptr, *d2 = nullptr, *inv_d1 = nullptr, *inv_d2 = nullptr;
+  T *c = nullptr, *lc = nullptr, *uc = nullptr, *lv = nullptr, *uv = nullptr;  // scaled
+  DevInputs orig;
+  double max_abs = 0.0;
+  double c_norm = 0.0, b_norm = 0.0;          // ||c||, ||Combine(lc,uc)|| of the unscaled LP
+  double c_norm_s = 0.0, b_norm_s = 0.0;      // same for the scaled LP
+  double* norm_part = nullptr;
+  unsigned int* norm_cnt = nullptr;
+  double* norm_out = nullptr;
+  int launches = 0;
+};
+
+template <class V, class T>
+static void norms2(Problem<T>& P, const V* c, const V* lc, const V* uc, double* out2,
+                   cudaStream_t s) {
+  const int G = std::max(1, std::min(num_sms() * 4, (int)vec_grid(std::max(P.m, P.n))));
+  k_norms<V><<<G, kThreads, 0, s>>>(c, lc, uc, P.m, P.n, P.norm_part, P.norm_cnt, P.norm_out);
+  PDLP_LAUNCH_CHECK();
+  P.launches++;
+  PDLP_CUDA_CHECK(cudaMemcpyAsync(out2, P.norm_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+}
+
+template <class T>
+static void build_problem(DeviceArena& arena, const Inputs& in, const DevInputs& d,
+                          int ruiz_iters, double pc_alpha, Problem<T>& P, cudaStream_t s) {
+  P.m = in.m;
+  P.n = in.n;
+  P.nnz = in.nnz;
+  P.orig = d;
+  const int64_t m = in.m, n = in.n, nnz = in.nnz;
+  P.norm_part = arena.alloc<double>(2 * num_sms() * 4);
+  P.norm_cnt = arena.alloc<unsigned int>(1);
+  P.norm_out = arena.alloc<double>(2);
+  PDLP_CUDA_CHECK(cudaMemsetAsync(P.norm_cnt, 0, sizeof(unsigned int), s));
+
+  // CSR of A and of its transpose (FP64 values while preconditioning)
+  P.A.rows = m;
+  P.A.cols = n;
+  P.A.nnz = nnz;
+  P.A.row_ptr = d.row_ptr;
+  P.A.col = d.col;
+  P.val64 = d.val;
+  P.AT.rows = n;
+  P.AT.cols = m;
+  P.AT.nnz = nnz;
+  P.AT.row_ptr = arena.alloc<int64_t>(n + 1);
+  P.AT.col = arena.alloc<int32_t>(nnz);
+  P.valT64 = arena.alloc<double>(nnz);
+  transpose_csr(arena, d.row_ptr, d.col, d.val, m, n, nnz, P.AT.row_ptr, P.AT.col, P.valT64, s);
+  P.launches += 10;
+
+  // Sec. 3: Ruiz passes, then Pock-Chambolle
+  P.d1 = arena.alloc<double>(m);
+  P.d2 = arena.alloc<double>(n);
+  double* nr = arena.alloc<double>(m);
+  double* nc = arena.alloc<double>(n);
+  double* fr = arena.alloc<double>(m);
+  double* fs = arena.alloc<double>(n);
+  k_fill<<<vec_grid(m), kThreads, 0, s>>>(P.d1, m, 1.0);
+  k_fill<<<vec_grid(n), kThreads, 0, s>>>(P.d2, n, 1.0);
+  PDLP_LAUNCH_CHECK();
+  auto pass = [&](int kind_r, double p_r, int kind_c, double p_c) {
+    row_norms(P.A.row_ptr, P.val64, m, kind_r, p_r, nr, s);
+    row_norms(P.AT.row_ptr, P.valT64, n, kind_c, p_c, nc, s);
+    scale_factors(nr, m, fr, P.d1, s);
+    scale_factors(nc, n, fs, P.d2, s);
+    scale_values(P.A.row_ptr, P.A.col, P.val64, m, fr, fs, false, s);
+    scale_values(P.AT.row_ptr, P.AT.col, P.valT64, n, fr, fs, true, s);
+    P.launches += 6;
+  };
+  for (int it = 0; it < ruiz_iters; ++it) pass(0, 0.0, 0, 0.0);
+  if (pc_alpha > 0.0) {
+    const double pr = 2.0 - pc_alpha, pcl = pc_alpha;
+    pass(pr == 1.0 ? 1 : 2, pr, pcl == 1.0 ? 1 : 2, pcl);
+  }
+  P.max_abs = max_abs(arena, P.val64, nnz, s);
+
+  // matrix values in the bulk precision
+  if (sizeof(T) == sizeof(double)) {
+    P.A.val = reinterpret_cast<T*>(P.val64);
+    P.AT.val = reinterpret_cast<T*>(P.valT64);
+  } else {
+    P.A.val = arena.alloc<T>(nnz);
+    P.AT.val = arena.alloc<T>(nnz);
+    convert_values<T>(P.val64, P.A.val, nnz, s);
+    convert_values<T>(P.valT64, P.AT.val, nnz, s);
+  }
+  build_tiles<T>(arena, P.A, s);
+  build_tiles<T>(arena, P.AT, s);
+
+  P.c = arena.alloc<T>(n);
+  P.lv = arena.alloc<T>(n);
+  P.uv = arena.alloc<T>(n);
+  P.lc = arena.alloc<T>(m);
+  P.uc = arena.alloc<T>(m);
+  P.inv_d1 = arena.alloc<double>(m);
+  P.inv_d2 = arena.alloc<double>(n);
+  k_scale_vectors<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(
+      d.c, d.lc, d.uc, d.lv, d.uv, P.d1, P.d2, m, n, P.c, P.lc, P.uc, P.lv, P.uv, P.inv_d1,
+      P.inv_d2);
+  PDLP_LAUNCH_CHECK();
+  double o2[2];
+  norms2<double, T>(P, d.c, d.lc, d.uc, o2, s);
+  P.c_norm = std::sqrt(o2[0]);
+  P.b_norm = std::sqrt(o2[1]);
+  norms2<T, T>(P, P.c, P.lc, P.uc, o2, s);
+  P.c_norm_s = std::sqrt(o2[0]);
+  P.b_norm_s = std::sqrt(o2[1]);
+}
+
+// ---------------------------------------------------------------------------
+// the solver
+// ---------------------------------------------------------------------------
+struct KktResult {
+  double rel_kkt, rel_primal, rel_dual, rel_gap, pres2, dres2, pres_inf, dres_inf, pobj, dobj,
+      paper_gap;
+};
+
+static KktResult kkt_finish(const KktSums& k, double c_norm, double b_norm) {
+  KktResult r;
+  r.pres2 = std::sqrt(k.pres2);
+  r.dres2 = std::sqrt(k.dres2);
+  r.pres_inf = k.pres_max;
+  r.dres_inf = k.dres_max;
+  r.pobj = k.pobj;
+  r.dobj = k.dobj_rows + k.dobj_cols;
+  r.rel_primal = r.pres2 / (1.0 + b_norm);
+  r.rel_dual = r.dres2 / (1.0 + c_norm);
+  r.rel_gap = std::fabs(r.pobj - r.dobj) / (1.0 + std::fabs(r.pobj) + std::fabs(r.dobj));
+  r.rel_kkt = std::max(r.rel_primal, std::max(r.rel_dual, r.rel_gap));
+  const double den = std::fabs(r.pobj) + std::fabs(r.dobj);
+  r.paper_gap = den > 0.0 ? std::fabs(r.pobj - r.dobj) / den : 0.0;
+  return r;
+}
+
+static bool converged(const KktResult& r, const pdlp_params& p) {
+  if (p.termination_mode == 0) return r.rel_kkt <= p.eps_rel_kkt;
+  return r.pres_inf <= p.eps_abs_feas && r.dres_inf <= p.eps_abs_feas && r.paper_gap <= p.eps_rel_gap;
+}
+
+using Clock = std::chrono::steady_clock;
+static double secs_since(Clock::time_point t0) {
+  return std::chrono::duration<double>(Clock::now() - t0).count();
+}
+
+struct EventTimer {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<int, int>> pending;  // (pair index, bucket)
+  size_t used = 0;
+  double ms[4] = {0, 0, 0, 0};
+  int64_t count[4] = {0, 0, 0, 0};
+  ~EventTimer() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+  int begin(cudaStream_t s) {
+    if (!on) return -1;
+    if (used + 2 > pool.size()) {
+      for (int i = 0; i < 64; ++i) {
+        cudaEvent_t e;
+        PDLP_CUDA_CHECK(cudaEventCreate(&e));
+        pool.push_back(e);
+      }
+    }
+    const int idx = (int)used;
+    used += 2;
+    PDLP_CUDA_CHECK(cudaEventRecord(pool[idx], s));
+    return idx;
+  }
+  void end(int idx, int bucket, cudaStream_t s) {
+    if (idx < 0) return;
+    PDLP_CUDA_CHECK(cudaEventRecord(pool[idx + 1], s));
+    pending.push_back({idx, bucket});
+  }
+  void collect() {  // after a stream synchronisation
+    for (auto& pr : pending) {
+      float t = 0.f;
+      PDLP_CUDA_CHECK(cudaEventElapsedTime(&t, pool[pr.first], pool[pr.first + 1]));
+      ms[pr.second] += t;
+      count[pr.second] += 1;
+    }
+    pending.clear();
+    used = 0;
+  }
+};
+
+template <class T>
+struct Solver {
+  const pdlp_params& prm;
+  cudaStream_t s;
+  DeviceArena arena;
+  Problem<T> P;
+  IterBuffers<T> b{};
+  T *X0 = nullptr, *Y0 = nullptr, *Xa = nullptr, *Ya = nullptr, *AXa = nullptr, *ATYa = nullptr;
+  DevState* dst = nullptr;
+  DevState hs{};
+  double *part_primal = nullptr, *part_dual = nullptr;
+  unsigned int* counters = nullptr;  // [0] spmv-A, [1] kkt, [2] gap, [3] dist2
+  int g_primal = 1, g_a = 1, g_at = 1, g_plain_a = 1, g_red = 1;
+  KktScratch kks{};
+  GapScratch gsc{};
+  double* dist_part = nullptr;
+  double* dist_out = nullptr;
+  EventTimer timer;
+  int64_t launches = 0;
+  double ms_checks = 0.0;
+
+  Solver(const pdlp_params& p, cudaStream_t st) : prm(p), s(st) {}
+
+  void alloc_iterates() {
+    const int64_t m = P.m, n = P.n;
+    for (int q = 0; q < 2; ++q) {
+      b.X[q] = arena.alloc<T>(n);
+      b.ATY[q] = arena.alloc<T>(n);
+      b.Y[q] = arena.alloc<T>(m);
+      b.AX[q] = arena.alloc<T>(m);
+    }
+    b.Sx = arena.alloc<T>(n);
+    b.SATy = arena.alloc<T>(n);
+    b.Sy = arena.alloc<T>(m);
+    b.SAx = arena.alloc<T>(m);
+    b.c = P.c;
+    b.lc = P.lc;
+    b.uc = P.uc;
+    b.lv = P.lv;
+    b.uv = P.uv;
+    b.m = m;
+    b.n = n;
+    X0 = arena.alloc<T>(n);
+    Y0 = arena.alloc<T>(m);
+    Xa = arena.alloc<T>(n);
+    ATYa = arena.alloc<T>(n);
+    Ya = arena.alloc<T>(m);
+    AXa = arena.alloc<T>(m);
+    dst = arena.alloc<DevState>(1);
+    g_primal = primal_grid(n);
+    g_a = spmv_grid<T>(P.A, kEpiDual);
+    g_at = spmv_grid<T>(P.AT, kEpiAverage);
+    g_plain_a = spmv_grid<T>(P.A, kEpiPlain);
+    g_red = std::max(1, num_sms() * 4);
+    part_primal = arena.alloc<double>(g_primal);
+    part_dual = arena.alloc<double>(2 * (int64_t)g_a);
+    counters = arena.alloc<unsigned int>(8);
+    PDLP_CUDA_CHECK(cudaMemsetAsync(counters, 0, 8 * sizeof(unsigned int), s));
+    kks.grid = g_red;
+    kks.part = arena.alloc<double>(7 * (int64_t)g_red);
+    kks.counter = counters + 1;
+    kks.out = arena.alloc<KktSums>(1);
+    gsc.grid = g_red;
+    gsc.ctx = static_cast<GapCtx*>(arena.alloc_bytes(gap_ctx_bytes()));
+    gsc.part = arena.alloc<double>((int64_t)kGapPartials * g_red);
+    gsc.counter = counters + 2;
+    gsc.cand = arena.alloc<int64_t>(kGapCandCap);
+    dist_part = arena.alloc<double>(2 * (int64_t)g_red);
+    dist_out = arena.alloc<double>(2);
+  }
+
+  void zero_sums() {
+    PDLP_CUDA_CHECK(cudaMemsetAsync(b.Sx, 0, sizeof(T) * P.n, s));
+    PDLP_CUDA_CHECK(cudaMemsetAsync(b.SATy, 0, sizeof(T) * P.n, s));
+    if (P.m) {
+      PDLP_CUDA_CHECK(cudaMemsetAsync(b.Sy, 0, sizeof(T) * P.m, s));
+      PDLP_CUDA_CHECK(cudaMemsetAsync(b.SAx, 0, sizeof(T) * P.m, s));
+    }
+  }
+
+  void push_state() {
+    PDLP_CUDA_CHECK(cudaMemcpyAsync(dst, &hs, sizeof(DevState), cudaMemcpyHostToDevice, s));
+  }
+  void pull_state() {
+    PDLP_CUDA_CHECK(cudaMemcpyAsync(&hs, dst, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+    timer.collect();
+  }
+
+  PointRef<T> current() const {
+    return PointRef<T>{b.X[hs.cur], b.Y[hs.cur], b.AX[hs.cur], b.ATY[hs.cur]};
+  }
+  PointRef<T> average() const { return PointRef<T>{Xa, Ya, AXa, ATYa}; }
+  ScaledVecs<T> scaled() const { return ScaledVecs<T>{P.c, P.lc, P.uc, P.lv, P.uv, P.m, P.n}; }
+  OrigVecs origv() const {
+    return OrigVecs{P.orig.c, P.orig.lc, P.orig.uc, P.orig.lv, P.orig.uv,
+                    P.d1,     P.d2,      P.inv_d1,  P.inv_d2};
+  }
+
+  double gap(const PointRef<T>& z, double omega) {
+    auto t0 = Clock::now();
+    int nl = 0;
+    const double mu = normalized_gap<T>(z, X0, Y0, omega, scaled(), gsc, s, &nl);
+    launches += nl;
+    ms_checks += 1e3 * secs_since(t0);
+    return mu;
+  }
+
+  KktResult kkt(const PointRef<T>& z) {
+    auto t0 = Clock::now();
+    launch_kkt<T>(z, origv(), P.m, P.n, kks, s);
+    launches++;
+    KktSums h;
+    PDLP_CUDA_CHECK(cudaMemcpyAsync(&h, kks.out, sizeof(KktSums), cudaMemcpyDeviceToHost, s));
+    PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+    ms_checks += 1e3 * secs_since(t0);
+    return kkt_finish(h, P.c_norm, P.b_norm);
+  }
+
+  // one step attempt = three launches (see file comment)
+  void launch_slot() {
+    int e0 = timer.begin(s);
+    launch_primal<T>(b, dst, part_primal, g_primal, s);
+    timer.end(e0, 2, s);
+    int e1 = timer.begin(s);
+    launch_spmv_dual<T>(P.A, b, dst, part_primal, g_primal, part_dual, counters, g_a, s);
+    timer.end(e1, 0, s);
+    int e2 = timer.begin(s);
+    launch_spmv_avg<T>(P.AT, b, dst, g_at, s);
+    timer.end(e2, 1, s);
+    launches += 3;
+  }
+
+  // first n (>= 1) such that restart condition (iii) t+j >= beta (k+j) holds
+  int64_t steps_to_artificial(int64_t k, int64_t t) const {
+    const double be = prm.beta_art;
+    int64_t j = 1;
+    if (be < 1.0) {
+      const double need = (be * (double)k - (double)t) / (1.0 - be);
+      if (need > 1.0) j = (int64_t)std::ceil(need);
+      while (j > 1 && (double)(t + j - 1) >= be * (double)(k + j - 1)) --j;
+      while (!((double)(t + j) >= be * (double)(k + j))) ++j;
+    } else {
+      j = std::numeric_limits<int64_t>::max() / 4;
+    }
+    return j;
+  }
+
+  int run(const Inputs& in, double* x_out, double* y_out, pdlp_stats* st) {
+    const auto t_start = Clock::now();
+    DevInputs d = stage_inputs(arena, in, s);
+    validate(arena, in, d, s);
+    build_problem<T>(arena, in, d, prm.ruiz_iters, prm.pc_alpha, P, s);
+    launches += P.launches;
+    alloc_iterates();
+    const int64_t m = P.m, n = P.n;
+
+    // z^{0,0} = (proj_X(0), 0)
+    k_init_point<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(P.lv, P.uv, b.X[0], b.Y[0],
+                                                                   b.ATY[0], X0, Y0, m, n);
+    PDLP_LAUNCH_CHECK();
+    launch_spmv_plain<T>(P.A, b.X[0], b.AX[0], g_plain_a, s);
+    launches += 2;
+    zero_sums();
+    const double eta0 = P.max_abs > 0.0 ? 1.0 / P.max_abs : 1.0;
+    const double omega0 = (P.c_norm_s > 0.0 && P.b_norm_s > 0.0) ? P.c_norm_s / P.b_norm_s : 1.0;
+    std::memset(&hs, 0, sizeof(hs));
+    hs.cur = 0;
+    hs.eta = eta0;
+    hs.eta_hat = eta0;
+    hs.omega = omega0;
+    hs.max_retries = prm.max_step_retries;
+    push_state();
+    PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+    const double t_setup = secs_since(t_start);
+    const auto t_solve0 = Clock::now();
+    timer.on = prm.profile != 0;
+
+    const int64_t period = std::max(1, prm.check_period);
+    const int64_t trace_iters = (prm.trace_out && prm.trace_iters > 0) ? prm.trace_iters : 0;
+    const int64_t rec_len = PDLP_TRACE_HEADER + n + m;
+    std::vector<T> hx, hy;
+
+    int status = -100;
+    int64_t restarts[3] = {0, 0, 0};
+    bool have_mu_ref = false;
+    double mu_ref = 0.0, mu_c_prev = INFINITY;
+    PointRef<T> out_pt = current();
+    KktResult out_k{};
+
+    // termination test on z^{0,0} before the first step
+    out_k = kkt(current());
+    if (converged(out_k, prm)) status = PDLP_OPTIMAL;
+
+    int64_t k = 0, t = 0, attempts_at_last = 0;
+    while (status == -100) {
+      const int64_t next_check = (k / period + 1) * period;
+      int64_t target = std::min(next_check, prm.max_iters);
+      const int64_t j_art = steps_to_artificial(k, t);
+      if (k + j_art < target) target = k + j_art;
+      // launch attempts until `target` accepted iterations (rejections need more)
+      bool error = false;
+      while (k < target) {
+        const int64_t need = (trace_iters > k) ? 1 : (target - k);
+        for (int64_t q = 0; q < need; ++q) launch_slot();
+        const double omega_used = hs.omega;
+        pull_state();
+        if (hs.error) {
+          error = true;
+          break;
+        }
+        if (trace_iters > k && hs.k > k) {
+          // record the accepted iteration hs.k (one slot per pull in trace mode)
+          double* rec = prm.trace_out + (size_t)k * rec_len;
+          rec[0] = (double)hs.k;
+          rec[1] = hs.eta_acc;
+          rec[2] = omega_used;
+          rec[3] = hs.eta_hat;
+          rec[4] = (double)(hs.attempts - attempts_at_last);
+          rec[5] = 0.0;
+          rec[6] = NAN;
+          rec[7] = NAN;
+          hx.resize(n);
+          hy.resize(m);
+          PDLP_CUDA_CHECK(cudaMemcpyAsync(hx.data(), b.X[hs.cur], sizeof(T) * n, cudaMemcpyDeviceToHost, s));
+          if (m) PDLP_CUDA_CHECK(cudaMemcpyAsync(hy.data(), b.Y[hs.cur], sizeof(T) * m, cudaMemcpyDeviceToHost, s));
+          PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+          for (int64_t j = 0; j < n; ++j) rec[PDLP_TRACE_HEADER + j] = (double)hx[j];
+          for (int64_t i = 0; i < m; ++i) rec[PDLP_TRACE_HEADER + n + i] = (double)hy[i];
+        }
+        if (hs.k > k) attempts_at_last = hs.attempts;
+        k = hs.k;
+        t = hs.t;
+      }
+      if (error) {
+        status = PDLP_NUMERICAL_ERROR;
+        out_pt = current();
+        out_k = kkt(out_pt);
+        break;
+      }
+      double* rec = (trace_iters >= k && k >= 1) ? prm.trace_out + (size_t)(k - 1) * rec_len : nullptr;
+      const bool is_check = (k % period) == 0;
+      const bool is_art = (double)t >= prm.beta_art * (double)k;
+      const bool is_limit = k >= prm.max_iters;
+      if (!(is_check || is_art || is_limit)) continue;
+      // GetRestartCandidate: current vs average since the restart
+      launch_average<T>(b.Sx, b.Sy, b.SAx, b.SATy, 1.0 / hs.W, P.lv, P.uv, Xa, Ya, AXa, ATYa, m, n, s);
+      launches++;
+      const double omega = hs.omega;
+      const double mu_cur = gap(current(), omega);
+      const double mu_avg = gap(average(), omega);
+      const bool cand_avg = !(mu_cur < mu_avg);
+      const double mu_c = cand_avg ? mu_avg : mu_cur;
+      const PointRef<T> cand = cand_avg ? average() : current();
+      if (rec) {
+        rec[6] = mu_cur;
+        rec[7] = mu_avg;
+      }
+      if (is_check || is_limit) {
+        out_k = kkt(cand);
+        if (prm.verbose)
+          std::fprintf(stderr, "pdlp: k=%lld rel_kkt=%.3e pobj=%.10e omega=%.3e eta=%.3e\n",
+                       (long long)k, out_k.rel_kkt, out_k.pobj, omega, hs.eta_hat);
+        if (converged(out_k, prm)) {
+          status = PDLP_OPTIMAL;
+          out_pt = cand;
+          break;
+        }
+        if (is_limit) {
+          status = PDLP_ITERATION_LIMIT;
+          out_pt = cand;
+          break;
+        }
+        if (secs_since(t_solve0) > prm.time_limit_s) {
+          status = PDLP_TIME_LIMIT;
+          out_pt = cand;
+          break;
+        }
+      }
+      int kind = 0;
+      if (is_check && have_mu_ref) {
+        if (mu_c <= prm.beta_suff * mu_ref)
+          kind = 1;
+        else if (mu_c <= prm.beta_nec * mu_ref && mu_c > mu_c_prev)
+          kind = 2;
+      }
+      if (kind == 0 && is_art) kind = 3;
+      if (is_check) mu_c_prev = mu_c;
+      if (kind == 0) continue;
+      // restart the outer loop at the candidate
+      restarts[kind - 1]++;
+      if (rec) rec[5] = (double)kind;
+      const int cur = hs.cur;
+      if (cand_avg) {
+        k_copy2<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(Xa, b.X[cur], n, Ya, b.Y[cur], m);
+        k_copy2<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(ATYa, b.ATY[cur], n, AXa, b.AX[cur], m);
+        PDLP_LAUNCH_CHECK();
+        launches += 2;
+      }
+      // Algorithm 3
+      launch_dist2<T>(b.X[cur], X0, b.Y[cur], Y0, m, n, dist_part, counters + 3, dist_out, g_red, s);
+      launches++;
+      double d2h[2];
+      PDLP_CUDA_CHECK(cudaMemcpyAsync(d2h, dist_out, sizeof(d2h), cudaMemcpyDeviceToHost, s));
+      PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+      const double dx = std::sqrt(d2h[0]), dy = std::sqrt(d2h[1]);
+      double om = hs.omega;
+      if (prm.eps_zero < dx && dx < 1.0 / prm.eps_zero && prm.eps_zero < dy && dy < 1.0 / prm.eps_zero)
+        om = std::exp(prm.theta * std::log(dy / dx) + (1.0 - prm.theta) * std::log(om));
+      mu_ref = gap(current(), om);
+      have_mu_ref = true;
+      k_copy2<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(b.X[cur], X0, n, b.Y[cur], Y0, m);
+      PDLP_LAUNCH_CHECK();
+      launches++;
+      zero_sums();
+      mu_c_prev = INFINITY;
+      hs.omega = om;
+      hs.W = 0.0;
+      hs.t = 0;
+      t = 0;
+      push_state();
+    }
+
+    // output: the returned point, unscaled
+    double* xo = x_out;
+    double* yo = y_out;
+    double* dx_out = nullptr;
+    double* dy_out = nullptr;
+    if (!in.on_device) {
+      dx_out = arena.alloc<double>(n);
+      dy_out = arena.alloc<double>(m);
+      xo = dx_out;
+      yo = dy_out;
+    }
+    k_unscale<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(out_pt.x, out_pt.y, P.d1, P.d2, xo, yo, m, n);
+    PDLP_LAUNCH_CHECK();
+    launches++;
+    if (!in.on_device) {
+      PDLP_CUDA_CHECK(cudaMemcpyAsync(x_out, dx_out, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+      if (m) PDLP_CUDA_CHECK(cudaMemcpyAsync(y_out, dy_out, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+    }
+    PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+    timer.collect();
+    if (st) {
+      std::memset(st, 0, sizeof(*st));
+      st->status = status;
+      st->iterations = hs.k;
+      st->attempts = hs.attempts;
+      st->rejected_steps = hs.rejected;
+      for (int q = 0; q < 3; ++q) st->restarts[q] = restarts[q];
+      st->kkt_passes = 0.5 * (double)(hs.attempts + hs.k);
+      st->rel_kkt = out_k.rel_kkt;
+      st->rel_primal = out_k.rel_primal;
+      st->rel_dual = out_k.rel_dual;
+      st->rel_gap = out_k.rel_gap;
+      st->primal_res_l2 = out_k.pres2;
+      st->dual_res_l2 = out_k.dres2;
+      st->primal_res_inf = out_k.pres_inf;
+      st->dual_res_inf = out_k.dres_inf;
+      st->pobj = out_k.pobj;
+      st->dobj = out_k.dobj;
+      st->paper_gap = out_k.paper_gap;
+      st->omega = hs.omega;
+      st->eta_hat = hs.eta_hat;
+      st->seconds_setup = t_setup;
+      st->seconds_solve = secs_since(t_solve0);
+      st->seconds_total = secs_since(t_start);
+      st->ms_spmv_a = timer.ms[0];
+      st->ms_spmv_at = timer.ms[1];
+      st->ms_primal = timer.ms[2];
+      st->ms_checks = ms_checks;
+      st->launches_spmv_a = timer.count[0];
+      st->launches_spmv_at = timer.count[1];
+      st->kernel_launches = launches;
+      const double v = (double)sizeof(T);
+      st->bytes_spmv_a = (double)(m + 1) * 8 + (double)P.nnz * (4 + v) + (double)n * v + 6.0 * m * v;
+      st->bytes_spmv_at = (double)(n + 1) * 8 + (double)P.nnz * (4 + v) + (double)m * v +
+                          6.0 * (double)n * v + 6.0 * (double)m * v;
+    }
+    return status;
+  }
+};
+
+static int handle_exception() {
+  try {
+    throw;
+  } catch (const PdlpError& e) {
+    set_last_error(e.what());
+    return e.code < 0 ? e.code : PDLP_NUMERICAL_ERROR;
+  } catch (const std::bad_alloc&) {
+    set_last_error("out of host memory");
+    return PDLP_OUT_OF_MEMORY;
+  } catch (const std::exception& e) {
+    set_last_error(e.what());
+    return PDLP_CUDA_ERROR;
+  } catch (...) {
+    set_last_error("unknown error");
+    return PDLP_CUDA_ERROR;
+  }
+}
+
+struct StreamGuard {
+  cudaStream_t s = nullptr;
+  bool own = false;
+  explicit StreamGuard(void* user) {
+    if (user) {
+      s = (cudaStream_t)user;
+    } else {
+      PDLP_CUDA_CHECK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+      own = true;
+    }
+  }
+  ~StreamGuard() {
+    if (own && s) {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+  }
+};
+
+static Inputs make_inputs(int64_t m, int64_t n, const pdlp_csr* A, const double* c,
+                          const double* lc, const double* uc, const double* lv, const double* uv,
+                          const pdlp_params* p) {
+  if (!A) throw PdlpError(-1, "A is NULL");
+  Inputs in;
+  in.m = m;
+  in.n = n;
+  in.nnz = A->nnz;
+  in.row_ptr = A->row_ptr;
+  in.col = A->col_idx;
+  in.val = A->val;
+  in.c = c;
+  in.lc = lc;
+  in.uc = uc;
+  in.lv = lv;
+  in.uv = uv;
+  in.on_device = p && p->inputs_on_device;
+  check_args(in);
+  return in;
+}
+
+}  // namespace pdlp
+
+using namespace pdlp;
+
+extern "C" {
+
+void pdlp_params_default(pdlp_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->eps_rel_kkt = 1e-8;
+  p->termination_mode = 0;
+  p->eps_abs_feas = 1e-8;
+  p->eps_rel_gap = 1e-2;
+  p->max_iters = 1000000000LL;
+  p->time_limit_s = INFINITY;
+  p->ruiz_iters = 10;
+  p->pc_alpha = 1.0;
+  p->check_period = 64;
+  p->beta_suff = 0.1;
+  p->beta_nec = 0.9;
+  p->beta_art = 0.5;
+  p->theta = 0.5;
+  p->eps_zero = 1e-10;
+  p->max_step_retries = 60;
+  p->precision = PDLP_FP64;
+  p->inputs_on_device = 0;
+  p->cuda_stream = nullptr;
+  p->trace_iters = 0;
+  p->trace_out = nullptr;
+  p->profile = 0;
+  p->verbose = 0;
+}
+
+const char* pdlp_last_error(void) { return g_last_error.c_str(); }
+
+int pdlp_solve(int64_t m, int64_t n, const pdlp_csr* A, const double* c, const double* lc,
+               const double* uc, const double* lv, const double* uv, const pdlp_params* p,
+               double* x_out, double* y_out, pdlp_stats* stats) {
+  try {
+    pdlp_params prm;
+    pdlp_params_default(&prm);
+    if (p) prm = *p;
+    const Inputs in = make_inputs(m, n, A, c, lc, uc, lv, uv, &prm);
+    if (!x_out || (m > 0 && !y_out)) throw PdlpError(-1, "null output array");
+    if (prm.pc_alpha >= 2.0) throw PdlpError(-1, "pc_alpha must be < 2");
+    if (prm.max_iters < 1 || prm.check_period < 1 || prm.max_step_retries < 1)
+      throw PdlpError(-1, "max_iters, check_period and max_step_retries must be >= 1");
+    StreamGuard sg(prm.cuda_stream);
+    if (prm.precision == PDLP_FP32_BULK) {
+      Solver<float> S(prm, sg.s);
+      return S.run(in, x_out, y_out, stats);
+    }
+    Solver<double> S(prm, sg.s);
+    return S.run(in, x_out, y_out, stats);
+  } catch (...) {
+    return handle_exception();
+  }
+}
+
+int pdlp_precondition(int64_t m, int64_t n, const pdlp_csr* A, const pdlp_params* p,
+                      double* d1_out, double* d2_out, double* scaled_val_out) {
+  try {
+    pdlp_params prm;
+    pdlp_params_default(&prm);
+    if (p) prm = *p;
+    // the vectors are not needed: use n zeros / unit bounds as placeholders
+    std::vector<double> zn((size_t)n, 0.0), on((size_t)n, 1.0), zm((size_t)m, 0.0);
+    Inputs in = make_inputs(m, n, A, zn.data(), zm.data(), zm.data(), zn.data(), on.data(), &prm);
+    StreamGuard sg(prm.cuda_stream);
+    cudaStream_t s = sg.s;
+    DeviceArena arena;
+    // stage the matrix from its own memory space and the placeholder vectors from host
+    Inputs mat = in;
+    DevInputs d;
+    d.row_ptr = arena.alloc<int64_t>(m + 1);
+    d.col = arena.alloc<int32_t>(in.nnz);
+    d.val = arena.alloc<double>(in.nnz);
+    copy_in(d.row_ptr, in.row_ptr, sizeof(int64_t) * (m + 1), in.on_device, s);
+    copy_in(d.col, in.col, sizeof(int32_t) * in.nnz, in.on_device, s);
+    copy_in(d.val, in.val, sizeof(double) * in.nnz, in.on_device, s);
+    mat.on_device = false;
+    d.c = arena.alloc<double>(n);
+    d.lv = arena.alloc<double>(n);
+    d.uv = arena.alloc<double>(n);
+    d.lc = arena.alloc<double>(m);
+    d.uc = arena.alloc<double>(m);
+    copy_in(d.c, zn.data(), sizeof(double) * n, false, s);
+    copy_in(d.lv, zn.data(), sizeof(double) * n, false, s);
+    copy_in(d.uv, on.data(), sizeof(double) * n, false, s);
+    copy_in(d.lc, zm.data(), sizeof(double) * m, false, s);
+    copy_in(d.uc, zm.data(), sizeof(double) * m, false, s);
+    validate(arena, mat, d, s);
+    Problem<double> P;
+    build_problem<double>(arena, mat, d, prm.ruiz_iters, prm.pc_alpha, P, s);
+    const cudaMemcpyKind k = in.on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (d1_out && m) PDLP_CUDA_CHECK(cudaMemcpyAsync(d1_out, P.d1, sizeof(double) * m, k, s));
+    if (d2_out) PDLP_CUDA_CHECK(cudaMemcpyAsync(d2_out, P.d2, sizeof(double) * n, k, s));
+    if (scaled_val_out && in.nnz)
+      PDLP_CUDA_CHECK(cudaMemcpyAsync(scaled_val_out, P.val64, sizeof(double) * in.nnz, k, s));
+    PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+    return 0;
+  } catch (...) {
+    return handle_exception();
+  }
+}
+
+// Shared by pdlp_normalized_gap and pdlp_kkt: stage the LP unscaled (no
+// preconditioning) and a point, compute A x and A'y with the SpMV engine.
+struct PointProblem {
+  DeviceArena arena;
+  Problem<double> P;
+  double *x, *y, *ax, *aty, *xr, *yr;
+};
+
+static void stage_point_problem(PointProblem& pp, const Inputs& in, const double* x,
+                                const double* y, const double* xr, const double* yr,
+                                cudaStream_t s) {
+  DevInputs d = stage_inputs(pp.arena, in, s);
+  validate(pp.arena, in, d, s);
+  build_problem<double>(pp.arena, in, d, 0, 0.0, pp.P, s);
+  const int64_t m = in.m, n = in.n;
+  pp.x = pp.arena.alloc<double>(n);
+  pp.y = pp.arena.alloc<double>(m);
+  pp.ax = pp.arena.alloc<double>(m);
+  pp.aty = pp.arena.alloc<double>(n);
+  copy_in(pp.x, x, sizeof(double) * n, in.on_device, s);
+  copy_in(pp.y, y, sizeof(double) * m, in.on_device, s);
+  pp.xr = pp.yr = nullptr;
+  if (xr) {
+    pp.xr = pp.arena.alloc<double>(n);
+    pp.yr = pp.arena.alloc<double>(m);
+    copy_in(pp.xr, xr, sizeof(double) * n, in.on_device, s);
+    copy_in(pp.yr, yr, sizeof(double) * m, in.on_device, s);
+  }
+  launch_spmv_plain<double>(pp.P.A, pp.x, pp.ax, spmv_grid<double>(pp.P.A, kEpiPlain), s);
+  if (m)
+    launch_spmv_plain<double>(pp.P.AT, pp.y, pp.aty, spmv_grid<double>(pp.P.AT, kEpiPlain), s);
+  else
+    PDLP_CUDA_CHECK(cudaMemsetAsync(pp.aty, 0, sizeof(double) * n, s));
+}
+
+int pdlp_normalized_gap(int64_t m, int64_t n, const pdlp_csr* A, const double* c,
+                        const double* lc, const double* uc, const double* lv,
+                        const double* uv, const double* x, const double* y,
+                        const double* x_ref, const double* y_ref, double omega,
+                        const pdlp_params* p, double* mu_out) {
+  try {
+    pdlp_params prm;
+    pdlp_params_default(&prm);
+    if (p) prm = *p;
+    const Inputs in = make_inputs(m, n, A, c, lc, uc, lv, uv, &prm);
+    if (!x || !x_ref || (m > 0 && (!y || !y_ref)) || !mu_out)
+      throw PdlpError(-1, "null point argument");
+    if (!(omega > 0.0) || !std::isfinite(omega)) throw PdlpError(-1, "omega must be positive");
+    StreamGuard sg(prm.cuda_stream);
+    PointProblem pp;
+    stage_point_problem(pp, in, x, y, x_ref, y_ref, sg.s);
+    const int g = std::max(1, num_sms() * 4);
+    GapScratch gsc;
+    gsc.grid = g;
+    gsc.ctx = static_cast<GapCtx*>(pp.arena.alloc_bytes(gap_ctx_bytes()));
+    gsc.part = pp.arena.alloc<double>((int64_t)kGapPartials * g);
+    gsc.counter = pp.arena.alloc<unsigned int>(1);
+    gsc.cand = pp.arena.alloc<int64_t>(kGapCandCap);
+    PDLP_CUDA_CHECK(cudaMemsetAsync(gsc.counter, 0, sizeof(unsigned int), sg.s));
+    const ScaledVecs<double> sv{pp.P.c, pp.P.lc, pp.P.uc, pp.P.lv, pp.P.uv, m, n};
+    *mu_out = normalized_gap<double>(PointRef<double>{pp.x, pp.y, pp.ax, pp.aty}, pp.xr, pp.yr,
+                                     omega, sv, gsc, sg.s, nullptr);
+    return 0;
+  } catch (...) {
+    return handle_exception();
+  }
+}
+
+int pdlp_kkt(int64_t m, int64_t n, const pdlp_csr* A, const double* c, const double* lc,
+             const double* uc, const double* lv, const double* uv, const double* x,
+             const double* y, const pdlp_params* p, double* out) {
+  try {
+    pdlp_params prm;
+    pdlp_params_default(&prm);
+    if (p) prm = *p;
+    const Inputs in = make_inputs(m, n, A, c, lc, uc, lv, uv, &prm);
+    if (!x || (m > 0 && !y) || !out) throw PdlpError(-1, "null point argument");
+    StreamGuard sg(prm.cuda_stream);
+    PointProblem pp;
+    stage_point_problem(pp, in, x, y, nullptr, nullptr, sg.s);
+    const int g = std::max(1, num_sms() * 4);
+    KktScratch ks;
+    ks.grid = g;
+    ks.part = pp.arena.alloc<double>(7 * (int64_t)g);
+    ks.counter = pp.arena.alloc<unsigned int>(1);
+    ks.out = pp.arena.alloc<KktSums>(1);
+    PDLP_CUDA_CHECK(cudaMemsetAsync(ks.counter, 0, sizeof(unsigned int), sg.s));
+    const OrigVecs o{pp.P.orig.c, pp.P.orig.lc, pp.P.orig.uc, pp.P.orig.lv, pp.P.orig.uv,
+                     pp.P.d1,     pp.P.d2,      pp.P.inv_d1,  pp.P.inv_d2};
+    launch_kkt<double>(PointRef<double>{pp.x, pp.y, pp.ax, pp.aty}, o, m, n, ks, sg.s);
+    KktSums h;
+    PDLP_CUDA_CHECK(cudaMemcpyAsync(&h, ks.out, sizeof(h), cudaMemcpyDeviceToHost, sg.s));
+    PDLP_CUDA_CHECK(cudaStreamSynchronize(sg.s));
+    const KktResult r = kkt_finish(h, pp.P.c_norm, pp.P.b_norm);
+    const double vals[11] = {r.rel_kkt,  r.rel_primal, r.rel_dual, r.rel_gap,
+                             r.pres2,    r.dres2,      r.pres_inf, r.dres_inf,
+                             r.pobj,     r.dobj,       r.paper_gap};
+    std::memcpy(out, vals, sizeof(vals));
+    return 0;
+  } catch (...) {
+    return handle_exception();
+  }
+}
+
+}  // extern "C"
