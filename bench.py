@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 PDLP library: PDHG iterations per second on the synthetic
+2,000,000 x 5,000,000 power-law LP (~5e7 nonzeros), FP64.
+
+One step = one pdlp_solve call on HBM-resident inputs that runs the whole path:
+preconditioning and transpose, a fixed number of PDHG iterations (adaptive step,
+both fused SpMVs, running averages), the periodic restart/termination checks and
+the unscaled output.  value = accepted iterations of all ranks / slowest rank's time.
+
+Also reported on the same JSON line:
+  e2e          the same metric through the C ABI with host (pinned) buffers, the
+               host<->device copies inside the timed region;
+  roofline     algorithmic bytes / CUDA-event time of the dominant fused SpMV kernel
+               against the measured HBM copy bandwidth;
+  cpu_baseline the FP64 CPU oracle on a bounded sample of the same workload;
+  time_to_rel_kkt_1e-4  wall clock of FP32-bulk and FP64 solves to relative KKT 1e-4,
+               with each result's errors measured by the oracle's KKT definitions.
+
+`--impl reference` times the CPU oracle instead (rank 0 only).
+Multi-GPU (torchrun): independent replicas, one instance per rank (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PDHG iters/s, HBM GB/s vs peak; time to rel-KKT 1e-4, FP32-bulk vs FP64"
+UNIT = "iters/s"
+PEAK_FALLBACK_GBS = 6800.0
+CPU_SAMPLE_ITERS = 12
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--iters-per-step", type=int, default=1000)
+    ap.add_argument("--scale", type=float, default=1.0, help="shrink the LP (testing only)")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--cpu-sample-child", action="store_true", help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def workload_name(inst):
+    return (f"powerlaw LP m={inst.m} n={inst.n} nnz={inst.nnz} (seeded synthetic: column "
+            f"degrees truncated power law on [2,5000] with mean 10, +-lognormal(0,1) values, "
+            f"40% equality rows, 10% free columns)")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return None
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for rel in ("paper_2501_07018_gb300/csrc/pdhg.cu", "paper_2501_07018_gb300/csrc/pdhg.cuh",
+                "paper_2501_07018_gb300/csrc/problem.cuh", "paper_2501_07018_gb300/csrc/common.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profiles(kernel_key, scale_units):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel source; null otherwise."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except OSError:
+        return None
+    e = t.get(kernel_key)
+    if not e or e.get("source_sha") != kernel_source_hash():
+        return None
+    return e["dram_bytes_per_launch"] * scale_units / e.get("units", scale_units)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle samples
+# ---------------------------------------------------------------------------
+def oracle_sample(inst, iters):
+    """`iters` PDHG iterations of the CPU oracle (Algorithm 2 step, A'y, running sums)
+    on the LP with identity scaling; returns seconds."""
+    import numpy as np
+    from oracle import pdlp_oracle as O
+
+    lp = O.precondition(inst, ruiz_iters=0, pc_alpha=0.0)
+    x = O.proj_box(np.zeros(inst.n), lp.lv, lp.uv)
+    y = np.zeros(inst.m)
+    Ax, ATy = lp.A @ x, lp.AT @ y
+    omega = O.initial_primal_weight(lp.c, lp.lc, lp.uc)
+    eta = 1.0 / float(np.max(np.abs(lp.A.data)))
+    Sx, Sy, SAx, SATy = np.zeros(inst.n), np.zeros(inst.m), np.zeros(inst.m), np.zeros(inst.n)
+    t0 = time.perf_counter()
+    for k in range(iters):
+        xn, yn, Axn, e, en, _, ok = O.adaptive_step(lp, x, y, Ax, ATy, omega, eta, k, 60)
+        ATyn = lp.AT @ yn
+        Sx += e * xn
+        Sy += e * yn
+        SAx += e * Axn
+        SATy += e * ATyn
+        x, y, Ax, ATy, eta = xn, yn, Axn, ATyn, en
+    return time.perf_counter() - t0
+
+
+def cpu_sample_child(args):
+    import lpgen
+
+    inst = lpgen.config1(scale=args.scale)
+    secs = oracle_sample(inst, CPU_SAMPLE_ITERS)
+    print(json.dumps({"secs": secs, "iters": CPU_SAMPLE_ITERS}))
+
+
+def cpu_baseline(args):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample-child", "--scale", str(args.scale)]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
+    line = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    if r.returncode != 0 or not line:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "failed: " + r.stderr[-300:]}
+    d = json.loads(line[-1])
+    return {"value": d["iters"] / d["secs"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"{d['iters']} PDHG iterations (Algorithm 2 step, A'y, running sums) of the "
+                       f"FP64 numpy/scipy oracle on the same LP with identity scaling, 1 thread, "
+                       f"{d['secs']:.1f} s; preconditioning and periodic checks excluded")}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(k, "1")
+    import lpgen
+
+    inst = lpgen.config1(scale=args.scale)
+    per_step = 2
+    for _ in range(args.warmup):
+        oracle_sample(inst, 1)
+    t = 0.0
+    for _ in range(args.steps):
+        t += oracle_sample(inst, per_step)
+    value = args.steps * per_step / t
+    sample = (f"{per_step} PDHG iterations per step of the FP64 numpy/scipy oracle on the same LP "
+              f"(identity scaling; preconditioning and periodic checks excluded), 1 thread")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": workload_name(inst), "iters_per_step": per_step},
+           "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1, "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import lpgen
+    import paper_2501_07018_gb300 as pkg
+
+    pkg.load_library()
+    inst = lpgen.config1(instance=rank, scale=args.scale)
+    dev = lambda a: torch.as_tensor(np.asarray(a)).cuda()  # noqa: E731
+    d = [dev(a) for a in (inst.row_ptr, inst.col_idx, inst.val, inst.c, inst.lc, inst.uc, inst.lv, inst.uv)]
+    stream = torch.cuda.current_stream()
+    iters = args.iters_per_step
+
+    def step(profile=1):
+        return pkg.solve(inst.m, inst.n, *d, max_iters=iters, eps_rel_kkt=0.0, profile=profile)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    agg = {"ms_spmv_a": 0.0, "ms_spmv_at": 0.0, "launches_spmv_a": 0, "launches_spmv_at": 0,
+           "kernel_launches": 0, "iterations": 0}
+    e0.record(stream)
+    last = None
+    for _ in range(args.steps):
+        r = step()
+        for k in agg:
+            agg[k] += r.stats[k]
+        last = r
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    secs = e0.elapsed_time(e1) / 1e3
+    t = torch.tensor([secs, float(agg["iterations"]), float(agg["kernel_launches"])], device="cuda",
+                     dtype=torch.float64)
+    if dist is not None:
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        secs_max, total_iters, total_launches = float(tmax[0]), float(t[1]), float(t[2])
+    else:
+        secs_max, total_iters, total_launches = secs, float(t[1]), float(t[2])
+    value = total_iters / secs_max
+
+    # dominant fused SpMV kernel (CUDA events inside the library, on the launching stream)
+    st = last.stats
+    cand = []
+    if agg["launches_spmv_a"]:
+        cand.append(("spmv_a", agg["ms_spmv_a"], agg["launches_spmv_a"], st["bytes_spmv_a"],
+                     "k_spmv<double,kEpiDual>: A x' + dual step (Eq. 3b) + step-size sums"))
+    if agg["launches_spmv_at"]:
+        cand.append(("spmv_at", agg["ms_spmv_at"], agg["launches_spmv_at"], st["bytes_spmv_at"],
+                     "k_spmv<double,kEpiAverage>: A'y' + running averages"))
+    key, ms, launches, bytes_per, desc = max(cand, key=lambda c: c[1])
+    per_launch_s = ms / launches / 1e3
+    achieved = bytes_per / per_launch_s / 1e9
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else PEAK_FALLBACK_GBS
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic_from_profiles(key, 1.0),
+                "kernel": desc, "algorithmic_bytes_per_launch": bytes_per,
+                "ms_per_launch": per_launch_s * 1e3,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"}
+    other = {c[0]: {"ms_per_launch": c[1] / c[2], "gbs": c[3] / (c[1] / c[2] / 1e3) / 1e9}
+             for c in cand}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * secs_max / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": workload_name(inst), "iters_per_step": iters,
+                      "precision": "fp64", "inputs": "HBM-resident (torch CUDA tensors)",
+                      "l2": "no flush: the matrix (A and A' ~1.2 GB FP64) is far larger than L2",
+                      "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+           "roofline": roofline, "kernels": other, "clocks": clocks,
+           "gpu_launches": int(total_launches)}
+
+    # e2e: host pinned buffers, copies inside the timed region
+    pinned = []
+    for a in (inst.row_ptr, inst.col_idx, inst.val, inst.c, inst.lc, inst.uc, inst.lv, inst.uv):
+        t_ = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        pinned.append(t_.numpy())
+    h2d = sum(a.nbytes for a in pinned)
+    d2h = 8 * (inst.n + inst.m)
+    e2e_steps = max(2, min(3, args.steps))
+    pkg.solve(inst.m, inst.n, *pinned, max_iters=iters, eps_rel_kkt=0.0)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        r = pkg.solve(inst.m, inst.n, *pinned, max_iters=iters, eps_rel_kkt=0.0)
+    t_e2e = time.perf_counter() - t0
+    tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    out["e2e"] = {"value": world * e2e_steps * iters / float(tt[0]), "unit": UNIT,
+                  "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                  "buffers": "pinned host memory via the C ABI (inputs_on_device = 0)"}
+
+    if rank == 0 and not args.no_extras:
+        out["time_to_rel_kkt_1e-4"] = time_to_tolerance(pkg, inst, d)
+        out["cpu_baseline"] = cpu_baseline(args)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def time_to_tolerance(pkg, inst, d):
+    """FP64 plain vs FP32 bulk to relative KKT 1e-4 on the same GPU; each result's
+    objective and residuals are re-measured by the oracle's FP64 KKT definitions."""
+    import torch
+    from oracle import pdlp_oracle as O
+
+    A = inst.scipy_csr()
+    res = {}
+    for name, prec in (("fp64", pkg.FP64), ("fp32_bulk", pkg.FP32_BULK)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = pkg.solve(inst.m, inst.n, *d, precision=prec, eps_rel_kkt=1e-4, max_iters=200000,
+                      time_limit_s=120.0)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        x, y = r.x.cpu().numpy(), r.y.cpu().numpy()
+        ok = O.kkt_stats(inst, A, x, y)
+        res[name] = {"seconds": wall, "status": r.status_name, "iterations": r.stats["iterations"],
+                     "seconds_setup": r.stats["seconds_setup"],
+                     "oracle_rel_kkt": ok["rel_kkt"], "oracle_rel_primal": ok["rel_primal"],
+                     "oracle_rel_dual": ok["rel_dual"], "oracle_rel_gap": ok["rel_gap"],
+                     "pobj": ok["pobj"], "primal_res_inf": ok["primal_res_inf"],
+                     "dual_res_inf": ok["dual_res_inf"]}
+    a, b = res["fp64"], res["fp32_bulk"]
+    res["fp32_vs_fp64_speedup"] = a["seconds"] / b["seconds"] if b["seconds"] > 0 else None
+    res["objective_rel_diff"] = abs(a["pobj"] - b["pobj"]) / max(abs(a["pobj"]), 1e-300)
+    return res
+
+
+def main():
+    args = parse_args()
+    if args.cpu_sample_child:
+        cpu_sample_child(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -117,6 +117,11 @@ typedef struct {
   int64_t launches_spmv_a, launches_spmv_at;
   int64_t kernel_launches; /* kernels of this library launched by the call         */
   double bytes_spmv_a, bytes_spmv_at; /* algorithmic bytes per launch              */
+  int64_t gap_evals;       /* normalized duality gap evaluations                   */
+  int64_t gap_fallbacks;   /* ... that needed the FP64 bracket scan                */
+  int64_t gap_failures;    /* ... left unresolved (mu treated as NaN: no restart by
+                              criteria (i)/(ii) at that check; pdlp_last_error()
+                              describes the last one)                              */
 } pdlp_stats;
 
 /* Fills *p with the defaults listed above. */

@@ -62,6 +62,8 @@ class Stats(ctypes.Structure):
         ("launches_spmv_a", ctypes.c_int64), ("launches_spmv_at", ctypes.c_int64),
         ("kernel_launches", ctypes.c_int64),
         ("bytes_spmv_a", ctypes.c_double), ("bytes_spmv_at", ctypes.c_double),
+        ("gap_evals", ctypes.c_int64), ("gap_fallbacks", ctypes.c_int64),
+        ("gap_failures", ctypes.c_int64),
     ]
 
     def as_dict(self):

@@ -21,6 +21,7 @@
 // If the FP32 scan mislocates the bracket or leaves too many breakpoints in it, the
 // host repeats the scan in FP64.
 #include <algorithm>
+#include <cstdio>
 #include <vector>
 
 #include "gap.cuh"
@@ -377,7 +378,9 @@ __global__ void __launch_bounds__(kThreads) k_gap_pass0(GapArgs<T> a, double ome
   if (c->r2 == 0.0) {
     c->mu = 0.0;
     c->state = kGapDone;
-  } else if (c->unb == 0 && c->dinf2 <= c->r2) {
+  } else if (c->unb == 0 && c->dinf2 <= c->r2 * (1.0 + 1e-12)) {
+    // every coordinate parks inside the ball (up to rounding): the maximiser is the
+    // fully saturated point
     c->mu = c->finf / c->r;
     c->state = kGapDone;
   } else if (!(c->slope2 > 0.0)) {
@@ -412,13 +415,14 @@ __global__ void __launch_bounds__(kThreads) k_gap_scan(GapArgs<T> a, int plan, i
   for (int q = 0; q < kGapQ; ++q) acc[q] = (Acc)0;
   const Acc omA = (Acc)om, iomA = (Acc)(1.0 / om);
   for (int64_t j = gi(); j < a.p.n; j += gs()) {
-    const Acc x = (Acc)a.z.x[j];
-    const Acc g = (Acc)a.p.c[j] - (Acc)a.z.aty[j];
-    if (g == (Acc)0) continue;
-    const Acc room = g > (Acc)0 ? x - (Acc)a.p.lv[j] : (Acc)a.p.uv[j] - x;
-    const Acc ga = g > (Acc)0 ? g : -g;
-    const Acc orm = omA * room;
-    const Acc sat = omA * room * room;
+    // g and the room to the bound in FP64 (both cancel near an optimum), then Acc
+    const double x = a.z.x[j];
+    const double g = (double)a.p.c[j] - (double)a.z.aty[j];
+    if (g == 0.0) continue;
+    const double room = g > 0.0 ? x - (double)a.p.lv[j] : (double)a.p.uv[j] - x;
+    const Acc ga = (Acc)fabs(g);
+    const Acc orm = (Acc)(om * room);
+    const Acc sat = (Acc)(om * room * room);
 #pragma unroll
     for (int q = 0; q < kGapQ; ++q) {
       const Acc t = pts[q] * ga;
@@ -545,7 +549,9 @@ __global__ void __launch_bounds__(kThreads) k_gap_exact(GapArgs<T> a) {
   c->d2lo = t[0] * slo * slo + t[1];
   c->d2hi = t[4];
   const int nc = ((volatile int*)&c->ncand)[0];
-  if (!(c->d2lo < c->r2 && c->d2hi >= c->r2) || nc > kGapCandCap) c->state = kGapFailed;
+  // the bracket must contain the crossing (up to rounding of the two summation orders)
+  const bool ok = c->d2lo < c->r2 * (1.0 + 1e-12) && c->d2hi >= c->r2 * (1.0 - 1e-12);
+  if (!ok || nc > kGapCandCap) c->state = kGapFailed;
 }
 
 // breakpoint value and coefficient change of one candidate
@@ -715,10 +721,17 @@ __global__ void k_gap_set(GapCtx* c, int state, int plan, double base_scale) {
 }
 __global__ void k_gap_clear_cand(GapCtx* c) { c->ncand = 0; }
 
+// bracket narrowed to rounding width: F at its left end from the exact coefficients
+__global__ void k_gap_degenerate(GapCtx* c) {
+  c->mu = (c->beta * c->s_lo + c->phi) / c->r;
+  c->state = kGapDone;
+}
+
 template <class T>
 double normalized_gap(const PointRef<T>& z, const T* x_ref, const T* y_ref, double omega,
                       const ScaledVecs<T>& p, const GapScratch& gsc, cudaStream_t s,
-                      int* launches) {
+                      int* launches, GapStats* stats) {
+  if (stats) stats->evals++;
   GapArgs<T> a;
   a.z = z;
   a.x_ref = x_ref;
@@ -744,6 +757,7 @@ double normalized_gap(const PointRef<T>& z, const T* x_ref, const T* y_ref, doub
   PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
   if (h.state != kGapDone) {
     // FP64 scan from the lower bound, octave block by octave block
+    if (stats) stats->fallbacks++;
     double scale = 1.0;
     for (int rep = 0; rep < 64; ++rep) {
       k_gap_set<<<1, 1, 0, s>>>(gsc.ctx, kGapActive, kPlanGeo, scale);
@@ -755,8 +769,7 @@ double normalized_gap(const PointRef<T>& z, const T* x_ref, const T* y_ref, doub
       if (h.state != kGapNeedMore) break;
       scale = ldexp(scale, kGapQ);
     }
-    if (h.state != kGapActive) throw PdlpError(5, "normalized duality gap: no bracket found");
-    for (int rep = 0; rep < 80; ++rep) {
+    for (int rep = 0; rep < 80 && h.state == kGapActive; ++rep) {
       k_gap_clear_cand<<<1, 1, 0, s>>>(gsc.ctx);
       k_gap_exact<T><<<G, kThreads, 0, s>>>(a);
       k_gap_finish<T><<<1, kThreads, 0, s>>>(a);
@@ -765,12 +778,32 @@ double normalized_gap(const PointRef<T>& z, const T* x_ref, const T* y_ref, doub
       PDLP_CUDA_CHECK(cudaMemcpyAsync(&h, gsc.ctx, sizeof(GapCtx), cudaMemcpyDeviceToHost, s));
       PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
       if (h.state == kGapDone) break;
+      if (h.s_hi - h.s_lo <= 1e-15 * h.s_hi) {
+        k_gap_degenerate<<<1, 1, 0, s>>>(gsc.ctx);
+        nl += 1;
+        PDLP_LAUNCH_CHECK();
+        PDLP_CUDA_CHECK(cudaMemcpyAsync(&h, gsc.ctx, sizeof(GapCtx), cudaMemcpyDeviceToHost, s));
+        PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+        break;
+      }
       k_gap_set<<<1, 1, 0, s>>>(gsc.ctx, kGapActive, kPlanLin, 1.0);
-      k_gap_scan<T, double><<<G, kThreads, 0, s>>>(a, kPlanLin, 0);
+      k_gap_scan<T, double><<<G, kThreads, 0, s>>>(a, kPlanLin, 1);
       nl += 2;
       PDLP_LAUNCH_CHECK();
     }
-    if (h.state != kGapDone) throw PdlpError(5, "normalized duality gap: bracket refinement failed");
+    if (h.state != kGapDone) {
+      char buf[320];
+      std::snprintf(buf, sizeof(buf),
+                    "normalized duality gap not resolved: state %d r2 %.17g s_lo %.17g s_hi %.17g "
+                    "d2lo %.17g d2hi %.17g ncand %d unb %d dinf2 %.17g",
+                    h.state, h.r2, h.s_lo, h.s_hi, h.d2lo, h.d2hi, h.ncand, h.unb, h.dinf2);
+      if (stats) {
+        stats->failures++;
+        stats->last_failure = buf;
+      }
+      if (launches) *launches += nl;
+      return NAN;
+    }
   }
   if (launches) *launches += nl;
   return h.mu;
@@ -781,7 +814,7 @@ double normalized_gap(const PointRef<T>& z, const T* x_ref, const T* y_ref, doub
                               const KktScratch&, cudaStream_t);                                 \
   template double normalized_gap<T>(const PointRef<T>&, const T*, const T*, double,             \
                                     const ScaledVecs<T>&, const GapScratch&, cudaStream_t,      \
-                                    int*);                                                      \
+                                    int*, GapStats*);                                           \
   template void launch_average<T>(const T*, const T*, const T*, const T*, double, const T*,     \
                                   const T*, T*, T*, T*, T*, int64_t, int64_t, cudaStream_t);    \
   template void launch_dist2<T>(const T*, const T*, const T*, const T*, int64_t, int64_t,       \

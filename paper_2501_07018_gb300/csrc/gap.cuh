@@ -2,6 +2,8 @@
 // normalized duality gap, and the restart helpers.
 #pragma once
 
+#include <string>
+
 #include "problem.cuh"
 
 namespace pdlp {
@@ -70,10 +72,17 @@ constexpr int kGapCandCap = 2048;
 constexpr int kGapPartials = kGapQ + 8;
 size_t gap_ctx_bytes();
 
+// Evaluation counters: `fallbacks` counts evaluations that needed the FP64 bracket
+// scan, `failures` those that could not be resolved (the result is then NaN and
+// `last_failure` describes the bracket).
+struct GapStats {
+  int64_t evals = 0, fallbacks = 0, failures = 0;
+  std::string last_failure;
+};
 template <class T>
 double normalized_gap(const PointRef<T>& z, const T* x_ref, const T* y_ref, double omega,
                       const ScaledVecs<T>& p, const GapScratch& gs, cudaStream_t s,
-                      int* launches);
+                      int* launches, GapStats* stats);
 
 // Helpers of the restart step and of the check: x_avg = S x / W etc. (clamped into the
 // box for x), copies, and sums of squared differences.

@@ -439,6 +439,7 @@ struct Solver {
   double* dist_part = nullptr;
   double* dist_out = nullptr;
   EventTimer timer;
+  GapStats gap_stats;
   int64_t launches = 0;
   double ms_checks = 0.0;
 
@@ -523,7 +524,7 @@ struct Solver {
   double gap(const PointRef<T>& z, double omega) {
     auto t0 = Clock::now();
     int nl = 0;
-    const double mu = normalized_gap<T>(z, X0, Y0, omega, scaled(), gsc, s, &nl);
+    const double mu = normalized_gap<T>(z, X0, Y0, omega, scaled(), gsc, s, &nl, &gap_stats);
     launches += nl;
     ms_checks += 1e3 * secs_since(t0);
     return mu;
@@ -796,6 +797,10 @@ struct Solver {
       st->launches_spmv_at = timer.count[1];
       st->kernel_launches = launches;
       const double v = (double)sizeof(T);
+      st->gap_evals = gap_stats.evals;
+      st->gap_fallbacks = gap_stats.fallbacks;
+      st->gap_failures = gap_stats.failures;
+      if (gap_stats.failures) set_last_error(gap_stats.last_failure);
       st->bytes_spmv_a = (double)(m + 1) * 8 + (double)P.nnz * (4 + v) + (double)n * v + 6.0 * m * v;
       st->bytes_spmv_at = (double)(n + 1) * 8 + (double)P.nnz * (4 + v) + (double)m * v +
                           6.0 * (double)n * v + 6.0 * (double)m * v;
@@ -1028,8 +1033,10 @@ int pdlp_normalized_gap(int64_t m, int64_t n, const pdlp_csr* A, const double* c
     gsc.cand = pp.arena.alloc<int64_t>(kGapCandCap);
     PDLP_CUDA_CHECK(cudaMemsetAsync(gsc.counter, 0, sizeof(unsigned int), sg.s));
     const ScaledVecs<double> sv{pp.P.c, pp.P.lc, pp.P.uc, pp.P.lv, pp.P.uv, m, n};
+    GapStats gst;
     *mu_out = normalized_gap<double>(PointRef<double>{pp.x, pp.y, pp.ax, pp.aty}, pp.xr, pp.yr,
-                                     omega, sv, gsc, sg.s, nullptr);
+                                     omega, sv, gsc, sg.s, nullptr, &gst);
+    if (gst.failures) throw PdlpError(-3, gst.last_failure);
     return 0;
   } catch (...) {
     return handle_exception();
