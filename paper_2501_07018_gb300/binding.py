@@ -234,6 +234,9 @@ def solve(m, n, row_ptr, col_idx, val, c, lc, uc, lv, uv, trace_iters: int = 0,
     st = Stats()
     code = lib.pdlp_solve(m, n, ctypes.byref(A), *vecs, ctypes.byref(prm), xp, yp, ctypes.byref(st))
     _check(code)
+    stats = st.as_dict()
+    if stats["gap_failures"]:
+        stats["gap_failure_message"] = lib.pdlp_last_error().decode()
     trace = []
     if trace_buf is not None:
         for row in trace_buf:
@@ -243,7 +246,7 @@ def solve(m, n, row_ptr, col_idx, val, c, lc, uc, lv, uv, trace_iters: int = 0,
                               attempts=int(row[4]), restart=int(row[5]), mu_cur=row[6],
                               mu_avg=row[7], x=row[TRACE_HEADER:TRACE_HEADER + n].copy(),
                               y=row[TRACE_HEADER + n:].copy()))
-    return SolveResult(code, x, y, st.as_dict(), trace)
+    return SolveResult(code, x, y, stats, trace)
 
 
 def solve_instance(inst, trace_iters: int = 0, device: bool = False, **params) -> SolveResult:

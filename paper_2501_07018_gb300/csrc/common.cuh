@@ -55,23 +55,23 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
-// Sums K values over the CTA (fixed tree: lanes, then warps in order).  The result is
-// valid in thread 0.  `scratch` needs K * kWarps doubles of shared memory.
-template <int K>
+// Sums K values over the CTA of NW warps (fixed tree: lanes, then warps in order).
+// The result is valid in thread 0.  `scratch` needs K * NW doubles of shared memory.
+template <int K, int NW = kWarps>
 __device__ __forceinline__ void block_sum(double (&v)[K], double* scratch) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
   if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) scratch[k * kWarps + warp] = v[k];
+    for (int k = 0; k < K; ++k) scratch[k * NW + warp] = v[k];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       double s = 0.0;
-      for (int w = 0; w < kWarps; ++w) s += scratch[k * kWarps + w];
+      for (int w = 0; w < NW; ++w) s += scratch[k * NW + w];
       v[k] = s;
     }
   }
@@ -95,12 +95,13 @@ __device__ __forceinline__ bool last_block_arrival(unsigned int* counter) {
   return s_last;
 }
 
-// Fixed-order sum of partials[0..count) by one CTA; result in thread 0.
+// Fixed-order sum of partials[0..count) by one CTA of NW warps; result in thread 0.
+template <int NW = kWarps>
 __device__ __forceinline__ double block_sum_array(const double* partials, int count,
                                                   double* scratch) {
   double v[1] = {0.0};
   for (int i = threadIdx.x; i < count; i += blockDim.x) v[0] += ((volatile const double*)partials)[i];
-  block_sum<1>(v, scratch);
+  block_sum<1, NW>(v, scratch);
   return v[0];
 }
 

@@ -5,9 +5,13 @@
 //                     yhat = y - sigma (2 A x' - A x)                       Eq. (3b)
 //                     + the step-size sums and, in the last CTA, the accept test
 //   k_spmv<kEpiAverage>  A'y' and the running sums of eta * (x, y, Ax, A'y)
-// Both sparse products share one tiled engine: a CTA stages a tile of rows (column
-// indices and values, kChunk entries at most) in shared memory, then groups of G
-// lanes reduce one row each; rows longer than kLongRow are split into chunks.
+// Both sparse products share one engine built on warp-sized work units: a warp loads
+// the column indices and values of its unit (<= 32 rows, <= kUnitCap nonzeros) and
+// gathers the source entries with all loads of a batch in flight, stages values and
+// gathered entries in its shared-memory slice, then every lane reduces one row in
+// element order (fused multiply-add, deterministic) and applies the row epilogue
+// with operands it prefetched when the unit started.  Rows longer than kLongRow are
+// split into kChunk-sized chunks.
 #include <algorithm>
 
 #include "pdhg.cuh"
@@ -86,18 +90,42 @@ struct EpiCtx {
   T* acc1;        // average: S A'y
 };
 
-// Row epilogue.  Returns the two step-size contributions for kEpiDual.
+// Epilogue operands of one row, loaded before its product is formed.
+template <class T>
+struct EpiIn {
+  T a, b, c, d;
+};
+
 template <class T, int EPI>
-__device__ __forceinline__ void row_epilogue(const EpiCtx<T>& e, int64_t row, T v, double& c0,
-                                             double& c1) {
+__device__ __forceinline__ EpiIn<T> load_epi(const EpiCtx<T>& e, int64_t row) {
+  EpiIn<T> r;
+  if (EPI == kEpiDual) {
+    r.a = e.in0[row];
+    r.b = e.in1[row];
+    r.c = e.lo[row];
+    r.d = e.hi[row];
+  } else if (EPI == kEpiAverage) {
+    r.a = e.in0[row];
+    r.b = e.acc0[row];
+    r.c = e.acc1[row];
+    r.d = (T)0;
+  } else {
+    r.a = r.b = r.c = r.d = (T)0;
+  }
+  return r;
+}
+
+// Row epilogue.  Accumulates the two step-size contributions for kEpiDual.
+template <class T, int EPI>
+__device__ __forceinline__ void row_epilogue(const EpiCtx<T>& e, const EpiIn<T>& in, int64_t row,
+                                             T v, double& c0, double& c1) {
   if (EPI == kEpiPlain) {
     e.out0[row] = v;
   } else if (EPI == kEpiDual) {
-    const T axo = e.in0[row];
-    const T yo = e.in1[row];
+    const T axo = in.a, yo = in.b;
     const T q = (T)2 * v - axo;
     const T yh = yo - e.sigma * q;
-    const T yn = yh - clampv<T>(yh, -e.sigma * e.hi[row], -e.sigma * e.lo[row]);
+    const T yn = yh - clampv<T>(yh, -e.sigma * in.d, -e.sigma * in.c);
     e.out0[row] = v;
     e.out1[row] = yn;
     const double dy = (double)yn - (double)yo;
@@ -106,44 +134,23 @@ __device__ __forceinline__ void row_epilogue(const EpiCtx<T>& e, int64_t row, T 
     c1 += dy * dax;
   } else {
     e.out0[row] = v;
-    e.acc0[row] += e.eta_acc * e.in0[row];
-    e.acc1[row] += e.eta_acc * v;
+    e.acc0[row] = in.b + e.eta_acc * in.a;
+    e.acc1[row] = in.c + e.eta_acc * v;
   }
 }
 
-template <class T>
-__device__ __forceinline__ T group_sum(T v, int G) {
-  for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
+constexpr int kSpmvWarps = 4;
+constexpr int kSpmvThreads = 32 * kSpmvWarps;
+constexpr int kSlices = kUnitCap / 32;
+constexpr int kBatch = 8;
 
-template <class T, int EPI, int G>
-__device__ __forceinline__ void tile_rows(const EpiCtx<T>& e, int64_t r0,
-                                          int nre, const int32_t* s_off, const int32_t* s_col,
-                                          const T* s_val, double& c0, double& c1) {
-  const int lane_g = threadIdx.x % G;
-  const int gid = threadIdx.x / G;
-  constexpr int ngroups = kThreads / G;
-  const T* __restrict__ src = e.src;
-  for (int base = 0; base < nre; base += ngroups) {
-    const int rr = base + gid;
-    T acc = (T)0;
-    if (rr < nre) {
-      const int pb = s_off[rr], pe = s_off[rr + 1];
-      for (int p = pb + lane_g; p < pe; p += G) acc += s_val[p] * src[s_col[p]];
-    }
-    if (G > 1) acc = group_sum<T>(acc, G);
-    if (rr < nre && lane_g == 0) row_epilogue<T, EPI>(e, r0 + rr, acc, c0, c1);
-  }
-}
-
+// Persistent kernel: warp w of the grid takes work items w, w + W, ... (W warps in
+// total).  Items [0, ntiles) are row units, the rest are chunks of long rows.
 template <class T, int EPI>
-__global__ void __launch_bounds__(kThreads) k_spmv(SpmvArgs<T> a) {
-  __shared__ int32_t s_off[kTileDiag + 1];
-  __shared__ int32_t s_col[kChunk];
-  __shared__ T s_val[kChunk];
-  __shared__ double red[2 * kWarps];
-  __shared__ int s_nre;
+__global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs<T> a) {
+  __shared__ T s_v[kSpmvWarps][kUnitCap];
+  __shared__ T s_x[kSpmvWarps][kUnitCap];
+  __shared__ double red[2 * kSpmvWarps];
 
   EpiCtx<T> e;
   e.sigma = (T)0;
@@ -191,39 +198,68 @@ __global__ void __launch_bounds__(kThreads) k_spmv(SpmvArgs<T> a) {
   }
 
   const Mat<T>& M = a.M;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  T* sv = s_v[wib];
+  T* sx = s_x[wib];
+  const T* __restrict__ src = e.src;
+  const int32_t* __restrict__ colp = M.col;
+  const T* __restrict__ valp = M.val;
   double c0 = 0.0, c1 = 0.0;
   const int64_t items = (int64_t)M.ntiles + M.nchunks;
-  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+  const int64_t W = (int64_t)gridDim.x * kSpmvWarps;
+  for (int64_t it = (int64_t)blockIdx.x * kSpmvWarps + wib; it < items; it += W) {
     if (it < M.ntiles) {
-      const int64_t r0 = M.tile_row[it], r1 = M.tile_row[it + 1];
-      const int nr = (int)(r1 - r0);
+      const int r0 = M.tile_row[it], r1 = M.tile_row[it + 1];
+      const int nr = r1 - r0;
       if (nr == 0) continue;
-      const int64_t nzb = M.row_ptr[r0];
-      for (int i = threadIdx.x; i <= nr; i += kThreads) s_off[i] = (int32_t)(M.row_ptr[r0 + i] - nzb);
-      __syncthreads();
-      if (threadIdx.x == 0) s_nre = (s_off[nr] - s_off[nr - 1] > kLongRow) ? nr - 1 : nr;
-      __syncthreads();
-      const int nre = s_nre;
-      const int nz = s_off[nre];
-      for (int p = threadIdx.x; p < nz; p += kThreads) {
-        s_col[p] = M.col[nzb + p];
-        s_val[p] = M.val[nzb + p];
+      const int64_t rs = lane < nr ? M.row_ptr[r0 + lane] : 0;
+      const int64_t re = lane < nr ? M.row_ptr[r0 + lane + 1] : 0;
+      const int64_t last_len = __shfl_sync(0xffffffffu, re - rs, nr - 1);
+      const int nre = last_len > kLongRow ? nr - 1 : nr;
+      const int64_t nzb = __shfl_sync(0xffffffffu, rs, 0);
+      const int64_t nze = nre > 0 ? __shfl_sync(0xffffffffu, re, nre - 1) : nzb;
+      const int nz = (int)(nze - nzb);
+      const bool own = lane < nre;
+      const int64_t row = r0 + lane;
+      EpiIn<T> ein{};
+      if (own) ein = load_epi<T, EPI>(e, row);
+      // stage the values and the gathered source entries of the unit
+      for (int b = 0; b < kSlices; b += kBatch) {
+        if (32 * b >= nz) break;
+        int cr[kBatch];
+        T vr[kBatch], xr[kBatch];
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+          const int p = 32 * (b + j) + lane;
+          cr[j] = 0;
+          vr[j] = (T)0;
+          if (p < nz) {
+            cr[j] = colp[nzb + p];
+            vr[j] = valp[nzb + p];
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+          const int p = 32 * (b + j) + lane;
+          xr[j] = p < nz ? src[cr[j]] : (T)0;
+        }
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+          const int p = 32 * (b + j) + lane;
+          if (p < nz) {
+            sv[p] = vr[j];
+            sx[p] = xr[j];
+          }
+        }
       }
-      __syncthreads();
-      const int avg = nre > 0 ? (nz + nre - 1) / nre : 1;
-      if (avg <= 2)
-        tile_rows<T, EPI, 1>(e, r0, nre, s_off, s_col, s_val, c0, c1);
-      else if (avg <= 4)
-        tile_rows<T, EPI, 2>(e, r0, nre, s_off, s_col, s_val, c0, c1);
-      else if (avg <= 8)
-        tile_rows<T, EPI, 4>(e, r0, nre, s_off, s_col, s_val, c0, c1);
-      else if (avg <= 16)
-        tile_rows<T, EPI, 8>(e, r0, nre, s_off, s_col, s_val, c0, c1);
-      else if (avg <= 48)
-        tile_rows<T, EPI, 16>(e, r0, nre, s_off, s_col, s_val, c0, c1);
-      else
-        tile_rows<T, EPI, 32>(e, r0, nre, s_off, s_col, s_val, c0, c1);
-      __syncthreads();
+      __syncwarp();
+      if (own) {
+        const int pb = (int)(rs - nzb), pe = (int)(re - nzb);
+        T acc = (T)0;
+        for (int p = pb; p < pe; ++p) acc = fma(sv[p], sx[p], acc);
+        row_epilogue<T, EPI>(e, ein, row, acc, c0, c1);
+      }
+      __syncwarp();
     } else {
       // one chunk of a long row
       const int64_t ci = it - M.ntiles;
@@ -235,11 +271,11 @@ __global__ void __launch_bounds__(kThreads) k_spmv(SpmvArgs<T> a) {
       const int64_t pb = rb + (ci - first) * kChunk;
       const int64_t pe = min(pb + (int64_t)kChunk, re);
       T acc = (T)0;
-      for (int64_t p = pb + threadIdx.x; p < pe; p += kThreads) acc += M.val[p] * e.src[M.col[p]];
-      double v[1] = {(double)acc};
-      block_sum<1>(v, red);
-      if (threadIdx.x == 0) {
-        M.long_part[ci] = v[0];
+#pragma unroll 4
+      for (int64_t p = pb + lane; p < pe; p += 32) acc = fma(valp[p], src[colp[p]], acc);
+      const double part = warp_sum((double)acc);
+      if (lane == 0) {
+        M.long_part[ci] = part;
         __threadfence();
         const unsigned prev = atomicAdd(&M.long_cnt[lr], 1u);
         if (prev == (unsigned)(nch - 1)) {
@@ -248,7 +284,8 @@ __global__ void __launch_bounds__(kThreads) k_spmv(SpmvArgs<T> a) {
           for (int64_t q = 0; q < nch; ++q) sum += ((volatile double*)M.long_part)[first + q];
           M.long_cnt[lr] = 0u;
           double d0 = 0.0, d1 = 0.0;
-          row_epilogue<T, EPI>(e, row, (T)sum, d0, d1);
+          const EpiIn<T> ein = load_epi<T, EPI>(e, row);
+          row_epilogue<T, EPI>(e, ein, row, (T)sum, d0, d1);
           if (EPI == kEpiDual) {
             M.long_contrib[2 * lr] = d0;
             M.long_contrib[2 * lr + 1] = d1;
@@ -262,22 +299,22 @@ __global__ void __launch_bounds__(kThreads) k_spmv(SpmvArgs<T> a) {
 
   // step-size sums: per CTA, then the last CTA reduces in fixed order and decides
   double v[2] = {c0, c1};
-  block_sum<2>(v, red);
+  block_sum<2, kSpmvWarps>(v, red);
   const int G = gridDim.x;
   if (threadIdx.x == 0) {
     a.part_dual[blockIdx.x] = v[0];
     a.part_dual[G + blockIdx.x] = v[1];
   }
   if (!last_block_arrival(a.counter)) return;
-  const double dx2 = block_sum_array(a.part_primal, a.grid_primal, red);
-  const double dy2_t = block_sum_array(a.part_dual, G, red);
-  const double in_t = block_sum_array(a.part_dual + G, G, red);
+  const double dx2 = block_sum_array<kSpmvWarps>(a.part_primal, a.grid_primal, red);
+  const double dy2_t = block_sum_array<kSpmvWarps>(a.part_dual, G, red);
+  const double in_t = block_sum_array<kSpmvWarps>(a.part_dual + G, G, red);
   double lc0[2] = {0.0, 0.0};
-  for (int i = threadIdx.x; i < M.nlong; i += kThreads) {
+  for (int i = threadIdx.x; i < M.nlong; i += blockDim.x) {
     lc0[0] += ((volatile double*)M.long_contrib)[2 * i];
     lc0[1] += ((volatile double*)M.long_contrib)[2 * i + 1];
   }
-  block_sum<2>(lc0, red);
+  block_sum<2, kSpmvWarps>(lc0, red);
   if (threadIdx.x != 0) return;
   const double dy2 = dy2_t + lc0[0];
   const double inter = in_t + lc0[1];
@@ -325,10 +362,10 @@ template <class T, int EPI>
 static int spmv_grid_impl(const Mat<T>& M) {
   static int occ = 0;
   if (occ == 0) {
-    PDLP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv<T, EPI>, kThreads, 0));
+    PDLP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv<T, EPI>, kSpmvThreads, 0));
     if (occ < 1) occ = 1;
   }
-  const int64_t items = M.work_items();
+  const int64_t items = (M.work_items() + kSpmvWarps - 1) / kSpmvWarps;
   const int64_t cap = (int64_t)num_sms() * occ;
   return (int)std::max<int64_t>(1, std::min(items, cap));
 }
@@ -363,7 +400,7 @@ void launch_spmv_dual(const Mat<T>& A, const IterBuffers<T>& b, DevState* st,
   a.grid_primal = grid_primal;
   a.part_dual = part_dual;
   a.counter = counter;
-  k_spmv<T, kEpiDual><<<grid, kThreads, 0, s>>>(a);
+  k_spmv<T, kEpiDual><<<grid, kSpmvThreads, 0, s>>>(a);
   PDLP_LAUNCH_CHECK();
 }
 
@@ -374,7 +411,7 @@ void launch_spmv_avg(const Mat<T>& AT, const IterBuffers<T>& b, DevState* st, in
   a.M = AT;
   a.b = b;
   a.st = st;
-  k_spmv<T, kEpiAverage><<<grid, kThreads, 0, s>>>(a);
+  k_spmv<T, kEpiAverage><<<grid, kSpmvThreads, 0, s>>>(a);
   PDLP_LAUNCH_CHECK();
 }
 
@@ -384,7 +421,7 @@ void launch_spmv_plain(const Mat<T>& M, const T* src, T* dst, int grid, cudaStre
   a.M = M;
   a.src = src;
   a.dst = dst;
-  k_spmv<T, kEpiPlain><<<grid, kThreads, 0, s>>>(a);
+  k_spmv<T, kEpiPlain><<<grid, kSpmvThreads, 0, s>>>(a);
   PDLP_LAUNCH_CHECK();
 }
 

@@ -8,18 +8,22 @@
 
 namespace pdlp {
 
-// Row tiling of a CSR matrix for the fused SpMV kernels.
-//   A "tile" is the set of rows whose merge-path coordinate r + row_ptr[r] falls in
-//   [t*kTileDiag, (t+1)*kTileDiag): at most kTileDiag rows and, excluding a long
-//   last row, fewer than kTileDiag + kLongRow nonzeros, so it fits the kChunk-entry
-//   shared-memory stage.  A row with more than kLongRow nonzeros is a "long row":
-//   it is always the last row of its tile, the tile skips it, and it is processed
-//   in kChunk-sized chunks by separate work items whose partial sums are combined,
-//   in chunk order, by the last chunk to finish.
-constexpr int kTileDiag = 1024;
-constexpr int kLongRow = 1024;
-constexpr int kChunk = 2048;
-static_assert(kTileDiag + kLongRow <= kChunk, "tile stage too small");
+// Row partition of a CSR matrix for the fused SpMV kernels.
+//   A "unit" is the work of one warp: the rows whose coordinate
+//   kUnitRowWeight * r + row_ptr[r] falls in [u*kUnitDiag, (u+1)*kUnitDiag).  A unit
+//   has at most kUnitDiag / kUnitRowWeight = 32 rows (one per lane) and, excluding a
+//   long last row, at most kUnitDiag - 1 + kLongRow nonzeros, which fit the warp's
+//   shared-memory stage of kUnitCap entries.  A row with more than kLongRow nonzeros is
+//   a "long row": it is always the last row of its unit, the unit skips it, and it is
+//   processed in kChunk-sized chunks by separate work items whose partial sums are
+//   combined, in chunk order, by the last chunk to finish.
+constexpr int kUnitRowWeight = 8;
+constexpr int kUnitDiag = 256;
+constexpr int kLongRow = 256;
+constexpr int kUnitCap = 512;
+constexpr int kChunk = 512;
+static_assert(kUnitDiag / kUnitRowWeight == 32, "one row per lane");
+static_assert(kUnitDiag - 1 + kLongRow <= kUnitCap, "unit stage too small");
 
 template <class T>
 struct Mat {
@@ -28,7 +32,7 @@ struct Mat {
   int32_t* col = nullptr;      // [nnz]
   T* val = nullptr;            // [nnz]
   int32_t ntiles = 0;
-  int32_t* tile_row = nullptr;     // [ntiles+1] first row of each tile
+  int32_t* tile_row = nullptr;     // [ntiles+1] first row of each unit
   int32_t nlong = 0;
   int32_t* long_rows = nullptr;    // [nlong]
   int64_t nchunks = 0;

@@ -446,11 +446,11 @@ __global__ void k_tile_rows(const int64_t* rp, int64_t rows, int64_t ntiles, int
       tile_row[t] = (int32_t)rows;
       continue;
     }
-    const int64_t target = t * kTileDiag;
-    int64_t lo = 0, hi = rows;  // first r with r + rp[r] >= target
+    const int64_t target = t * kUnitDiag;
+    int64_t lo = 0, hi = rows;  // first r with kUnitRowWeight * r + rp[r] >= target
     while (lo < hi) {
       const int64_t mid = (lo + hi) >> 1;
-      if (mid + rp[mid] >= target)
+      if (kUnitRowWeight * mid + rp[mid] >= target)
         hi = mid;
       else
         lo = mid + 1;
@@ -493,7 +493,7 @@ void build_tiles(DeviceArena& arena, Mat<T>& M, cudaStream_t s) {
   PDLP_CUDA_CHECK(cudaMemcpyAsync(&last_start, M.row_ptr + (M.rows - 1), sizeof(int64_t),
                                   cudaMemcpyDeviceToHost, s));
   PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
-  const int64_t ntiles = (M.rows - 1 + last_start) / kTileDiag + 1;
+  const int64_t ntiles = (kUnitRowWeight * (M.rows - 1) + last_start) / kUnitDiag + 1;
   if (ntiles > INT32_MAX - 1) throw PdlpError(-1, "matrix too large for the row tiling");
   M.ntiles = (int32_t)ntiles;
   M.tile_row = arena.alloc<int32_t>(ntiles + 1);

@@ -122,10 +122,12 @@ __global__ void k_copy2(const T* a, T* a_out, int64_t na, const T* b, T* b_out, 
   for (int64_t i = sgi(); i < nb; i += sgs()) b_out[i] = b[i];
 }
 
+// x = D2 x~ (kept inside [lv, uv] against the rounding of the product), y = D1 y~
 template <class T>
-__global__ void k_unscale(const T* x, const T* y, const double* d1, const double* d2, double* xo,
-                          double* yo, int64_t m, int64_t n) {
-  for (int64_t j = sgi(); j < n; j += sgs()) xo[j] = d2[j] * (double)x[j];
+__global__ void k_unscale(const T* x, const T* y, const double* d1, const double* d2,
+                          const double* lv, const double* uv, double* xo, double* yo, int64_t m,
+                          int64_t n) {
+  for (int64_t j = sgi(); j < n; j += sgs()) xo[j] = fmin(fmax(d2[j] * (double)x[j], lv[j]), uv[j]);
   for (int64_t i = sgi(); i < m; i += sgs()) yo[i] = d1[i] * (double)y[i];
 }
 
@@ -756,7 +758,8 @@ struct Solver {
       xo = dx_out;
       yo = dy_out;
     }
-    k_unscale<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(out_pt.x, out_pt.y, P.d1, P.d2, xo, yo, m, n);
+    k_unscale<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(out_pt.x, out_pt.y, P.d1, P.d2,
+                                                               P.orig.lv, P.orig.uv, xo, yo, m, n);
     PDLP_LAUNCH_CHECK();
     launches++;
     if (!in.on_device) {

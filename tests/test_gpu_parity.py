@@ -79,6 +79,7 @@ def test_solve_objective_at_rel_kkt_1e8(pkg, name):
     assert own["rel_kkt"] <= 1.01e-8
     assert abs(own["pobj"] - res.stats["pobj"]) <= 1e-9 * abs(own["pobj"])
     assert np.all(res.x >= inst.lv) and np.all(res.x <= inst.uv)
+    assert res.stats["gap_failures"] == 0, res.stats.get("gap_failure_message")
 
 
 def test_host_and_device_inputs_identical(pkg):
