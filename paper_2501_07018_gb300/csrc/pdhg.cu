@@ -378,8 +378,9 @@ int spmv_grid(const Mat<T>& M, int epi) {
 }
 
 int primal_grid(int64_t n) {
-  const int64_t need = (n + kThreads * 4 - 1) / (kThreads * 4);
-  return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 4));
+  // about two elements per thread: enough independent loads in flight per SM
+  const int64_t need = (n + kThreads * 2 - 1) / (kThreads * 2);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 64));
 }
 
 template <class T>
