@@ -5,13 +5,13 @@
 //                     yhat = y - sigma (2 A x' - A x)                       Eq. (3b)
 //                     + the step-size sums and, in the last CTA, the accept test
 //   k_spmv<kEpiAverage>  A'y' and the running sums of eta * (x, y, Ax, A'y)
-// Both sparse products share one engine built on warp-sized work units: a warp loads
-// the column indices and values of its unit (<= 32 rows, <= kUnitCap nonzeros) and
-// gathers the source entries with all loads of a batch in flight, stages values and
-// gathered entries in its shared-memory slice, then every lane reduces one row in
-// element order (fused multiply-add, deterministic) and applies the row epilogue
-// with operands it prefetched when the unit started.  Rows longer than kLongRow are
-// split into kChunk-sized chunks.
+// Both sparse products share one engine over the SELL-32 layout of problem.cuh: a
+// warp owns a slice of 32 rows of nearly equal length (rows are numbered by length),
+// one row per lane; it streams the slice's entries k-major (coalesced), keeps a batch
+// of loads and gathers in flight, accumulates its row with fused multiply-adds in
+// entry order (deterministic) and applies the row epilogue with operands prefetched
+// when the slice started.  Every FP64 instruction thus runs with all 32 lanes active,
+// which matters on GB300 where the FP64 pipe is narrow.  Long rows go in chunks.
 #include <algorithm>
 
 #include "pdhg.cuh"
@@ -21,14 +21,35 @@ namespace pdlp {
 __device__ __forceinline__ int64_t gtid2() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ int64_t gstride2() { return (int64_t)gridDim.x * blockDim.x; }
 
+// Monotone integer key of a non-NaN double: signed comparison of the keys orders the
+// values like IEEE comparison (with -0 < +0).  Clamping doubles through the integer
+// pipe keeps the scarce FP64 pipe of GB300 for arithmetic.
+__device__ __forceinline__ long long dkey(double v) {
+  const long long b = __double_as_longlong(v);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
 template <class T>
-__device__ __forceinline__ T clampv(T v, T lo, T hi) {
-  return fmin(fmax(v, lo), hi);
+__device__ __forceinline__ T clampv(T v, T lo, T hi);
+template <>
+__device__ __forceinline__ double clampv<double>(double v, double lo, double hi) {
+  const long long kv = dkey(v);
+  return kv < dkey(lo) ? lo : (kv > dkey(hi) ? hi : v);
 }
 template <>
 __device__ __forceinline__ float clampv<float>(float v, float lo, float hi) {
   return fminf(fmaxf(v, lo), hi);
 }
+
+// Accumulator type of the per-lane step-size sums: FP64 for the FP64 path, FP32 for
+// FP32 bulk (converted to FP64 for the cross-lane reduction).
+template <class T>
+struct AccT {
+  using type = double;
+};
+template <>
+struct AccT<float> {
+  using type = float;
+};
 
 // ---------------------------------------------------------------------------
 // Eq. (3a)
@@ -39,7 +60,8 @@ __global__ void __launch_bounds__(kThreads) k_primal(IterBuffers<T> b, DevState*
   const int cur = st->cur;
   const bool err = st->error != 0;
   const double eta = st->eta, omega = st->omega;
-  double acc[1] = {0.0};
+  using A = typename AccT<T>::type;
+  A lacc = (A)0;
   if (!err) {
     const T tau = (T)(eta / omega);
     const T* __restrict__ x = b.X[cur];
@@ -49,10 +71,11 @@ __global__ void __launch_bounds__(kThreads) k_primal(IterBuffers<T> b, DevState*
       const T xo = x[j];
       const T v = clampv<T>(xo - tau * (b.c[j] - aty[j]), b.lv[j], b.uv[j]);
       xn[j] = v;
-      const double d = (double)v - (double)xo;
-      acc[0] += d * d;
+      const A d = (A)v - (A)xo;
+      lacc = fma(d, d, lacc);
     }
   }
+  double acc[1] = {(double)lacc};
   block_sum<1>(acc, red);
   if (threadIdx.x == 0) part[blockIdx.x] = acc[0];
 }
@@ -116,9 +139,9 @@ __device__ __forceinline__ EpiIn<T> load_epi(const EpiCtx<T>& e, int64_t row) {
 }
 
 // Row epilogue.  Accumulates the two step-size contributions for kEpiDual.
-template <class T, int EPI>
+template <class T, int EPI, class A>
 __device__ __forceinline__ void row_epilogue(const EpiCtx<T>& e, const EpiIn<T>& in, int64_t row,
-                                             T v, double& c0, double& c1) {
+                                             T v, A& c0, A& c1) {
   if (EPI == kEpiPlain) {
     e.out0[row] = v;
   } else if (EPI == kEpiDual) {
@@ -128,10 +151,10 @@ __device__ __forceinline__ void row_epilogue(const EpiCtx<T>& e, const EpiIn<T>&
     const T yn = yh - clampv<T>(yh, -e.sigma * in.d, -e.sigma * in.c);
     e.out0[row] = v;
     e.out1[row] = yn;
-    const double dy = (double)yn - (double)yo;
-    const double dax = (double)v - (double)axo;
-    c0 += dy * dy;
-    c1 += dy * dax;
+    const A dy = (A)yn - (A)yo;
+    const A dax = (A)v - (A)axo;
+    c0 = fma(dy, dy, c0);
+    c1 = fma(dy, dax, c1);
   } else {
     e.out0[row] = v;
     e.acc0[row] = in.b + e.eta_acc * in.a;
@@ -141,16 +164,14 @@ __device__ __forceinline__ void row_epilogue(const EpiCtx<T>& e, const EpiIn<T>&
 
 constexpr int kSpmvWarps = 4;
 constexpr int kSpmvThreads = 32 * kSpmvWarps;
-constexpr int kSlices = kUnitCap / 32;
 constexpr int kBatch = 8;
 
 // Persistent kernel: warp w of the grid takes work items w, w + W, ... (W warps in
-// total).  Items [0, ntiles) are row units, the rest are chunks of long rows.
+// total).  Items [0, nchunks) are chunks of the long rows, the rest are SELL slices.
 template <class T, int EPI>
 __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs<T> a) {
-  __shared__ T s_v[kSpmvWarps][kUnitCap];
-  __shared__ T s_x[kSpmvWarps][kUnitCap];
   __shared__ double red[2 * kSpmvWarps];
+  using A = typename AccT<T>::type;
 
   EpiCtx<T> e;
   e.sigma = (T)0;
@@ -199,77 +220,49 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs<T> a) {
 
   const Mat<T>& M = a.M;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  T* sv = s_v[wib];
-  T* sx = s_x[wib];
   const T* __restrict__ src = e.src;
-  const int32_t* __restrict__ colp = M.col;
-  const T* __restrict__ valp = M.val;
-  double c0 = 0.0, c1 = 0.0;
-  const int64_t items = (int64_t)M.ntiles + M.nchunks;
+  A c0 = (A)0, c1 = (A)0;
+  const int64_t items = M.nchunks + M.nslices;
   const int64_t W = (int64_t)gridDim.x * kSpmvWarps;
   for (int64_t it = (int64_t)blockIdx.x * kSpmvWarps + wib; it < items; it += W) {
-    if (it < M.ntiles) {
-      const int r0 = M.tile_row[it], r1 = M.tile_row[it + 1];
-      const int nr = r1 - r0;
-      if (nr == 0) continue;
-      const int64_t rs = lane < nr ? M.row_ptr[r0 + lane] : 0;
-      const int64_t re = lane < nr ? M.row_ptr[r0 + lane + 1] : 0;
-      const int64_t last_len = __shfl_sync(0xffffffffu, re - rs, nr - 1);
-      const int nre = last_len > kLongRow ? nr - 1 : nr;
-      const int64_t nzb = __shfl_sync(0xffffffffu, rs, 0);
-      const int64_t nze = nre > 0 ? __shfl_sync(0xffffffffu, re, nre - 1) : nzb;
-      const int nz = (int)(nze - nzb);
-      const bool own = lane < nre;
-      const int64_t row = r0 + lane;
+    if (it >= M.nchunks) {
+      // one SELL slice: 32 rows, one per lane, entries k-major
+      const int64_t sl = it - M.nchunks;
+      const int64_t row = (int64_t)M.R0 + 32 * sl + lane;
+      const bool own = row < M.rows;
       EpiIn<T> ein{};
       if (own) ein = load_epi<T, EPI>(e, row);
-      // stage the values and the gathered source entries of the unit
-      for (int b = 0; b < kSlices; b += kBatch) {
-        if (32 * b >= nz) break;
+      const int L = M.slice_len[sl];
+      const int32_t* __restrict__ cp = M.sell_col + M.slice_ptr[sl] + lane;
+      const T* __restrict__ vp = M.sell_val + M.slice_ptr[sl] + lane;
+      T acc = (T)0;
+      for (int k0 = 0; k0 < L; k0 += kBatch) {
         int cr[kBatch];
         T vr[kBatch], xr[kBatch];
 #pragma unroll
-        for (int j = 0; j < kBatch; ++j) {
-          const int p = 32 * (b + j) + lane;
-          cr[j] = 0;
-          vr[j] = (T)0;
-          if (p < nz) {
-            cr[j] = colp[nzb + p];
-            vr[j] = valp[nzb + p];
-          }
+        for (int u = 0; u < kBatch; ++u) {
+          const bool in = k0 + u < L;
+          cr[u] = in ? cp[32 * (k0 + u)] : 0;
+          vr[u] = in ? vp[32 * (k0 + u)] : (T)0;
         }
 #pragma unroll
-        for (int j = 0; j < kBatch; ++j) {
-          const int p = 32 * (b + j) + lane;
-          xr[j] = p < nz ? src[cr[j]] : (T)0;
-        }
+        for (int u = 0; u < kBatch; ++u) xr[u] = (k0 + u < L) ? src[cr[u]] : (T)0;
 #pragma unroll
-        for (int j = 0; j < kBatch; ++j) {
-          const int p = 32 * (b + j) + lane;
-          if (p < nz) {
-            sv[p] = vr[j];
-            sx[p] = xr[j];
-          }
-        }
+        for (int u = 0; u < kBatch; ++u)
+          if (k0 + u < L) acc = fma(vr[u], xr[u], acc);
       }
-      __syncwarp();
-      if (own) {
-        const int pb = (int)(rs - nzb), pe = (int)(re - nzb);
-        T acc = (T)0;
-        for (int p = pb; p < pe; ++p) acc = fma(sv[p], sx[p], acc);
-        row_epilogue<T, EPI>(e, ein, row, acc, c0, c1);
-      }
-      __syncwarp();
+      if (own) row_epilogue<T, EPI, A>(e, ein, row, acc, c0, c1);
     } else {
-      // one chunk of a long row
-      const int64_t ci = it - M.ntiles;
-      const int lr = M.chunk_owner[ci];
-      const int64_t row = M.long_rows[lr];
-      const int64_t first = M.chunk_ptr[lr];
-      const int64_t nch = M.chunk_ptr[lr + 1] - first;
+      // one chunk of a long row (CSR)
+      const int64_t ci = it;
+      const int64_t row = M.chunk_owner[ci];
+      const int64_t first = M.chunk_ptr[row];
+      const int64_t nch = M.chunk_ptr[row + 1] - first;
       const int64_t rb = M.row_ptr[row], re = M.row_ptr[row + 1];
       const int64_t pb = rb + (ci - first) * kChunk;
       const int64_t pe = min(pb + (int64_t)kChunk, re);
+      const int32_t* __restrict__ colp = M.col;
+      const T* __restrict__ valp = M.val;
       T acc = (T)0;
 #pragma unroll 4
       for (int64_t p = pb + lane; p < pe; p += 32) acc = fma(valp[p], src[colp[p]], acc);
@@ -277,18 +270,18 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs<T> a) {
       if (lane == 0) {
         M.long_part[ci] = part;
         __threadfence();
-        const unsigned prev = atomicAdd(&M.long_cnt[lr], 1u);
+        const unsigned prev = atomicAdd(&M.long_cnt[row], 1u);
         if (prev == (unsigned)(nch - 1)) {
           __threadfence();
           double sum = 0.0;
           for (int64_t q = 0; q < nch; ++q) sum += ((volatile double*)M.long_part)[first + q];
-          M.long_cnt[lr] = 0u;
-          double d0 = 0.0, d1 = 0.0;
+          M.long_cnt[row] = 0u;
+          A d0 = (A)0, d1 = (A)0;
           const EpiIn<T> ein = load_epi<T, EPI>(e, row);
-          row_epilogue<T, EPI>(e, ein, row, (T)sum, d0, d1);
+          row_epilogue<T, EPI, A>(e, ein, row, (T)sum, d0, d1);
           if (EPI == kEpiDual) {
-            M.long_contrib[2 * lr] = d0;
-            M.long_contrib[2 * lr + 1] = d1;
+            M.long_contrib[2 * row] = (double)d0;
+            M.long_contrib[2 * row + 1] = (double)d1;
           }
         }
       }
@@ -298,7 +291,7 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs<T> a) {
   if (EPI != kEpiDual) return;
 
   // step-size sums: per CTA, then the last CTA reduces in fixed order and decides
-  double v[2] = {c0, c1};
+  double v[2] = {(double)c0, (double)c1};
   block_sum<2, kSpmvWarps>(v, red);
   const int G = gridDim.x;
   if (threadIdx.x == 0) {
@@ -310,7 +303,7 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs<T> a) {
   const double dy2_t = block_sum_array<kSpmvWarps>(a.part_dual, G, red);
   const double in_t = block_sum_array<kSpmvWarps>(a.part_dual + G, G, red);
   double lc0[2] = {0.0, 0.0};
-  for (int i = threadIdx.x; i < M.nlong; i += blockDim.x) {
+  for (int i = threadIdx.x; i < M.R0; i += blockDim.x) {
     lc0[0] += ((volatile double*)M.long_contrib)[2 * i];
     lc0[1] += ((volatile double*)M.long_contrib)[2 * i + 1];
   }
@@ -365,7 +358,7 @@ static int spmv_grid_impl(const Mat<T>& M) {
     PDLP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv<T, EPI>, kSpmvThreads, 0));
     if (occ < 1) occ = 1;
   }
-  const int64_t items = (M.work_items() + kSpmvWarps - 1) / kSpmvWarps;
+  const int64_t items = (M.work_items() + kSpmvWarps - 1) / kSpmvWarps;  // warps -> CTAs
   const int64_t cap = (int64_t)num_sms() * occ;
   return (int)std::max<int64_t>(1, std::min(items, cap));
 }

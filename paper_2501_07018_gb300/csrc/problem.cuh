@@ -8,40 +8,39 @@
 
 namespace pdlp {
 
-// Row partition of a CSR matrix for the fused SpMV kernels.
-//   A "unit" is the work of one warp: the rows whose coordinate
-//   kUnitRowWeight * r + row_ptr[r] falls in [u*kUnitDiag, (u+1)*kUnitDiag).  A unit
-//   has at most kUnitDiag / kUnitRowWeight = 32 rows (one per lane) and, excluding a
-//   long last row, at most kUnitDiag - 1 + kLongRow nonzeros, which fit the warp's
-//   shared-memory stage of kUnitCap entries.  A row with more than kLongRow nonzeros is
-//   a "long row": it is always the last row of its unit, the unit skips it, and it is
-//   processed in kChunk-sized chunks by separate work items whose partial sums are
-//   combined, in chunk order, by the last chunk to finish.
-constexpr int kUnitRowWeight = 8;
-constexpr int kUnitDiag = 256;
+// Storage of a (row- and column-renumbered) sparse matrix for the fused SpMV kernels.
+//   Rows are numbered by decreasing length.  The first R0 rows (every row longer than
+//   kLongRow, rounded up to a multiple of 32) stay in CSR and are processed in chunks
+//   of kChunk entries, one warp per chunk; chunk partial sums of a row are combined
+//   in chunk order by the last chunk to finish.  The remaining rows are stored as
+//   SELL-32: slice s holds rows R0 + 32 s ... R0 + 32 s + 31, padded to the length of
+//   its first (longest) row, entry k of lane l at slice_ptr[s] + 32 k + l; padding
+//   entries have value 0.  One warp processes one slice, one row per lane.
 constexpr int kLongRow = 256;
-constexpr int kUnitCap = 512;
 constexpr int kChunk = 512;
-static_assert(kUnitDiag / kUnitRowWeight == 32, "one row per lane");
-static_assert(kUnitDiag - 1 + kLongRow <= kUnitCap, "unit stage too small");
 
 template <class T>
 struct Mat {
   int64_t rows = 0, cols = 0, nnz = 0;
+  // CSR of the renumbered matrix (only its first R0 rows are read by the kernels)
   int64_t* row_ptr = nullptr;  // [rows+1]
   int32_t* col = nullptr;      // [nnz]
   T* val = nullptr;            // [nnz]
-  int32_t ntiles = 0;
-  int32_t* tile_row = nullptr;     // [ntiles+1] first row of each unit
-  int32_t nlong = 0;
-  int32_t* long_rows = nullptr;    // [nlong]
+  int32_t R0 = 0;
   int64_t nchunks = 0;
-  int64_t* chunk_ptr = nullptr;    // [nlong+1] first chunk of each long row
-  int32_t* chunk_owner = nullptr;  // [nchunks] long-row index of each chunk
-  unsigned int* long_cnt = nullptr;  // [nlong] arrival counters (kept at 0 between launches)
+  int64_t* chunk_ptr = nullptr;      // [R0+1] first chunk of each long row
+  int32_t* chunk_owner = nullptr;    // [nchunks] row of each chunk
+  unsigned int* long_cnt = nullptr;  // [R0] arrival counters (kept at 0 between launches)
   double* long_part = nullptr;       // [nchunks] chunk partial sums
-  double* long_contrib = nullptr;    // [nlong * 2] per-long-row reduction contributions
-  int64_t work_items() const { return (int64_t)ntiles + nchunks; }
+  double* long_contrib = nullptr;    // [R0 * 2] per-long-row reduction contributions
+  // SELL-32 of rows [R0, rows)
+  int64_t nslices = 0;
+  int64_t* slice_ptr = nullptr;  // [nslices+1]
+  int32_t* slice_len = nullptr;  // [nslices]
+  int32_t* sell_col = nullptr;
+  T* sell_val = nullptr;
+  int64_t sell_entries = 0;
+  int64_t work_items() const { return nchunks + nslices; }
 };
 
 // Simple owning list of device allocations, freed together.
@@ -108,8 +107,20 @@ void scale_values(const int64_t* row_ptr, const int32_t* col, double* val, int64
                   cudaStream_t s);
 double max_abs(DeviceArena& arena, const double* v, int64_t len, cudaStream_t s);
 
+// Permutation sorting `count` rows by decreasing length (ties by index): perm[new] = old,
+// inv[old] = new.  Lengths come from a row-pointer array.
+void sort_by_length_desc(DeviceArena& arena, const int64_t* row_ptr, int64_t count,
+                         int32_t* perm, int32_t* inv, cudaStream_t s);
+// Renumbered CSR: new row r holds old row perm_r[r] with column c renamed inv_c[c]
+// (entry order kept).
+void permute_csr(DeviceArena& arena, const int64_t* row_ptr, const int32_t* col,
+                 const double* val, int64_t rows, const int32_t* perm_r, const int32_t* inv_c,
+                 int64_t* new_row_ptr, int32_t* new_col, double* new_val, cudaStream_t s);
+// Chunk list of the long rows and the SELL-32 copy of the rest (values converted to T).
 template <class T>
-void build_tiles(DeviceArena& arena, Mat<T>& M, cudaStream_t s);
+void build_sell(DeviceArena& arena, Mat<T>& M, const double* val64, cudaStream_t s);
+// out[i] = in[perm[i]]
+void gather_f64(const double* in, const int32_t* perm, double* out, int64_t len, cudaStream_t s);
 template <class T>
 void convert_values(const double* src, T* dst, int64_t len, cudaStream_t s);
 

@@ -286,6 +286,46 @@ __global__ void k_iota64(int64_t* v, int64_t n) {
   for (int64_t i = gtid(); i < n; i += gstride()) v[i] = i;
 }
 
+// Stable LSD radix sort of non-negative int32 keys < 2^bits; returns the sorted
+// positions (the original index of each sorted entry) in a fresh array.
+static int64_t* radix_sort_positions(DeviceArena& arena, const int32_t* keys, int64_t N, int bits,
+                                     cudaStream_t s) {
+  const int passes = (bits + 7) / 8;
+  const int64_t ntiles = std::max<int64_t>(1, (N + kRsTile - 1) / kRsTile);
+  int32_t* kbuf[2] = {arena.alloc<int32_t>(N), arena.alloc<int32_t>(N)};
+  int64_t* vbuf[2] = {arena.alloc<int64_t>(N), arena.alloc<int64_t>(N)};
+  if (N == 0) return vbuf[0];
+  int64_t* hist = arena.alloc<int64_t>(256 * ntiles);
+  int64_t* offs = arena.alloc<int64_t>(256 * ntiles + 1);
+  const int32_t* kin = keys;
+  const int64_t* vin = nullptr;  // identity payload on the first pass
+  int which = 0;
+  for (int ps = 0; ps < passes; ++ps) {
+    const int shift = 8 * ps;
+    k_rs_hist<<<(unsigned)ntiles, kThreads, 0, s>>>(kin, N, shift, hist, ntiles);
+    PDLP_LAUNCH_CHECK();
+    exclusive_scan_i64(arena, hist, offs, 256 * ntiles, s);
+    k_rs_scatter<<<(unsigned)ntiles, kThreads, 0, s>>>(kin, vin, kbuf[which], vbuf[which], N,
+                                                       shift, offs, ntiles);
+    PDLP_LAUNCH_CHECK();
+    kin = kbuf[which];
+    vin = vbuf[which];
+    which ^= 1;
+  }
+  if (passes == 0) {
+    k_iota64<<<grid_for(N), kThreads, 0, s>>>(vbuf[0], N);
+    PDLP_LAUNCH_CHECK();
+    return vbuf[0];
+  }
+  return const_cast<int64_t*>(vin);
+}
+
+static int bits_for(int64_t maxval) {
+  int bits = 0;
+  while (bits < 62 && ((int64_t)1 << bits) <= maxval) ++bits;
+  return bits;
+}
+
 void transpose_csr(DeviceArena& arena, const int64_t* row_ptr, const int32_t* col,
                    const double* val, int64_t m, int64_t n, int64_t nnz, int64_t* t_row_ptr,
                    int32_t* t_col, double* t_val, cudaStream_t s) {
@@ -298,41 +338,101 @@ void transpose_csr(DeviceArena& arena, const int64_t* row_ptr, const int32_t* co
   }
   exclusive_scan_i64(arena, reinterpret_cast<const int64_t*>(cnt), t_row_ptr, n, s);
   if (nnz == 0) return;
-
   int32_t* rowidx = arena.alloc<int32_t>(nnz);
   k_expand_rows<<<grid_for(m * 32), kThreads, 0, s>>>(row_ptr, m, rowidx);
   PDLP_LAUNCH_CHECK();
+  const int64_t* perm = radix_sort_positions(arena, col, nnz, bits_for(n - 1), s);
+  k_gather_transpose<<<grid_for(nnz), kThreads, 0, s>>>(perm, rowidx, val, nnz, t_col, t_val);
+  PDLP_LAUNCH_CHECK();
+}
 
-  int bits = 0;
-  while (bits < 63 && ((int64_t)1 << bits) < n) ++bits;
-  const int passes = (bits + 7) / 8;
-  const int64_t ntiles = (nnz + kRsTile - 1) / kRsTile;
-  int32_t* kbuf[2] = {arena.alloc<int32_t>(nnz), arena.alloc<int32_t>(nnz)};
-  int64_t* vbuf[2] = {arena.alloc<int64_t>(nnz), arena.alloc<int64_t>(nnz)};
-  int64_t* hist = arena.alloc<int64_t>(256 * ntiles);
-  int64_t* offs = arena.alloc<int64_t>(256 * ntiles + 1);
-  const int32_t* kin = col;
-  const int64_t* vin = nullptr;  // identity payload on the first pass
-  int which = 0;
-  for (int ps = 0; ps < passes; ++ps) {
-    const int shift = 8 * ps;
-    k_rs_hist<<<(unsigned)ntiles, kThreads, 0, s>>>(kin, nnz, shift, hist, ntiles);
-    PDLP_LAUNCH_CHECK();
-    exclusive_scan_i64(arena, hist, offs, 256 * ntiles, s);
-    k_rs_scatter<<<(unsigned)ntiles, kThreads, 0, s>>>(kin, vin, kbuf[which], vbuf[which], nnz,
-                                                       shift, offs, ntiles);
-    PDLP_LAUNCH_CHECK();
-    kin = kbuf[which];
-    vin = vbuf[which];
-    which ^= 1;
+// ---------------------------------------------------------------------------
+// renumbering by row length
+// ---------------------------------------------------------------------------
+__global__ void k_len_keys(const int64_t* rp, int64_t rows, int64_t maxlen, int32_t* key) {
+  for (int64_t i = gtid(); i < rows; i += gstride()) key[i] = (int32_t)(maxlen - (rp[i + 1] - rp[i]));
+}
+__global__ void k_max_len(const int64_t* rp, int64_t rows, unsigned long long* out) {
+  unsigned long long mx = 0;
+  for (int64_t i = gtid(); i < rows; i += gstride()) {
+    const unsigned long long l = (unsigned long long)(rp[i + 1] - rp[i]);
+    mx = l > mx ? l : mx;
   }
-  if (passes == 0) {
-    // n == 1: every key is 0 and the input order is already the stable order
-    k_iota64<<<grid_for(nnz), kThreads, 0, s>>>(vbuf[0], nnz);
-    PDLP_LAUNCH_CHECK();
-    vin = vbuf[0];
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = t > mx ? t : mx;
   }
-  k_gather_transpose<<<grid_for(nnz), kThreads, 0, s>>>(vin, rowidx, val, nnz, t_col, t_val);
+  if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
+}
+__global__ void k_perm_from_positions(const int64_t* pos, int64_t n, int32_t* perm, int32_t* inv) {
+  for (int64_t i = gtid(); i < n; i += gstride()) {
+    const int64_t o = pos[i];
+    perm[i] = (int32_t)o;
+    inv[o] = (int32_t)i;
+  }
+}
+
+void sort_by_length_desc(DeviceArena& arena, const int64_t* rp, int64_t count, int32_t* perm,
+                         int32_t* inv, cudaStream_t s) {
+  if (count == 0) return;
+  unsigned long long* mx = arena.alloc<unsigned long long>(1);
+  PDLP_CUDA_CHECK(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s));
+  k_max_len<<<grid_for(count), kThreads, 0, s>>>(rp, count, mx);
+  PDLP_LAUNCH_CHECK();
+  unsigned long long hmx = 0;
+  PDLP_CUDA_CHECK(cudaMemcpyAsync(&hmx, mx, sizeof(hmx), cudaMemcpyDeviceToHost, s));
+  PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+  int32_t* key = arena.alloc<int32_t>(count);
+  k_len_keys<<<grid_for(count), kThreads, 0, s>>>(rp, count, (int64_t)hmx, key);
+  PDLP_LAUNCH_CHECK();
+  const int64_t* pos = radix_sort_positions(arena, key, count, bits_for((int64_t)hmx), s);
+  k_perm_from_positions<<<grid_for(count), kThreads, 0, s>>>(pos, count, perm, inv);
+  PDLP_LAUNCH_CHECK();
+}
+
+__global__ void k_perm_lens(const int64_t* rp, const int32_t* perm, int64_t rows, int64_t* len) {
+  for (int64_t i = gtid(); i < rows; i += gstride()) {
+    const int32_t o = perm[i];
+    len[i] = rp[o + 1] - rp[o];
+  }
+}
+__global__ void k_perm_rows(const int64_t* rp, const int32_t* col, const double* val,
+                            const int32_t* perm, const int32_t* inv_c, int64_t rows,
+                            const int64_t* nrp, int32_t* ncol, double* nval) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = gtid() >> 5, nwarps = gstride() >> 5;
+  for (int64_t i = warp; i < rows; i += nwarps) {
+    const int32_t o = perm[i];
+    const int64_t b = rp[o], len = rp[o + 1] - b, nb = nrp[i];
+    for (int64_t k = lane; k < len; k += 32) {
+      ncol[nb + k] = inv_c[col[b + k]];
+      nval[nb + k] = val[b + k];
+    }
+  }
+}
+
+void permute_csr(DeviceArena& arena, const int64_t* rp, const int32_t* col, const double* val,
+                 int64_t rows, const int32_t* perm_r, const int32_t* inv_c, int64_t* nrp,
+                 int32_t* ncol, double* nval, cudaStream_t s) {
+  int64_t* len = arena.alloc<int64_t>(rows);
+  if (rows) {
+    k_perm_lens<<<grid_for(rows), kThreads, 0, s>>>(rp, perm_r, rows, len);
+    PDLP_LAUNCH_CHECK();
+  }
+  exclusive_scan_i64(arena, len, nrp, rows, s);
+  if (rows) {
+    k_perm_rows<<<grid_for(rows * 32), kThreads, 0, s>>>(rp, col, val, perm_r, inv_c, rows, nrp,
+                                                         ncol, nval);
+    PDLP_LAUNCH_CHECK();
+  }
+}
+
+__global__ void k_gather_f64(const double* in, const int32_t* perm, double* out, int64_t len) {
+  for (int64_t i = gtid(); i < len; i += gstride()) out[i] = in[perm[i]];
+}
+void gather_f64(const double* in, const int32_t* perm, double* out, int64_t len, cudaStream_t s) {
+  if (len == 0) return;
+  k_gather_f64<<<grid_for(len), kThreads, 0, s>>>(in, perm, out, len);
   PDLP_LAUNCH_CHECK();
 }
 
@@ -438,101 +538,114 @@ double max_abs(DeviceArena& arena, const double* v, int64_t len, cudaStream_t s)
 }
 
 // ---------------------------------------------------------------------------
-// row tiling for the fused SpMV kernels
+// long-row chunks and SELL-32 for the fused SpMV kernels
 // ---------------------------------------------------------------------------
-__global__ void k_tile_rows(const int64_t* rp, int64_t rows, int64_t ntiles, int32_t* tile_row) {
-  for (int64_t t = gtid(); t <= ntiles; t += gstride()) {
-    if (t == ntiles) {
-      tile_row[t] = (int32_t)rows;
-      continue;
-    }
-    const int64_t target = t * kUnitDiag;
-    int64_t lo = 0, hi = rows;  // first r with kUnitRowWeight * r + rp[r] >= target
-    while (lo < hi) {
-      const int64_t mid = (lo + hi) >> 1;
-      if (kUnitRowWeight * mid + rp[mid] >= target)
-        hi = mid;
-      else
-        lo = mid + 1;
-    }
-    tile_row[t] = (int32_t)lo;
-  }
+__global__ void k_count_long(const int64_t* rp, int64_t rows, unsigned long long* cnt) {
+  unsigned long long c = 0;
+  for (int64_t i = gtid(); i < rows; i += gstride()) c += (rp[i + 1] - rp[i] > kLongRow) ? 1ull : 0ull;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(cnt, c);
 }
-
-__global__ void k_long_flags(const int64_t* rp, int64_t rows, int64_t* flag, int64_t* nch) {
-  for (int64_t i = gtid(); i < rows; i += gstride()) {
+__global__ void k_chunk_counts(const int64_t* rp, int64_t R0, int64_t* nch) {
+  for (int64_t i = gtid(); i < R0; i += gstride()) {
     const int64_t len = rp[i + 1] - rp[i];
-    const bool lng = len > kLongRow;
-    flag[i] = lng ? 1 : 0;
-    nch[i] = lng ? (len + kChunk - 1) / kChunk : 0;
+    nch[i] = len > 0 ? (len + kChunk - 1) / kChunk : 1;
   }
 }
-
-__global__ void k_long_compact(const int64_t* flag, const int64_t* pos, const int64_t* nch,
-                               const int64_t* nch_pos, int64_t rows, int32_t* long_rows,
-                               int64_t* chunk_ptr, int32_t* chunk_owner) {
-  for (int64_t i = gtid(); i < rows; i += gstride()) {
-    if (!flag[i]) continue;
-    const int64_t lr = pos[i];
-    long_rows[lr] = (int32_t)i;
-    chunk_ptr[lr] = nch_pos[i];
-    for (int64_t c = 0; c < nch[i]; ++c) chunk_owner[nch_pos[i] + c] = (int32_t)lr;
+__global__ void k_chunk_owner(const int64_t* chunk_ptr, int64_t R0, int32_t* owner) {
+  for (int64_t i = gtid(); i < R0; i += gstride())
+    for (int64_t c = chunk_ptr[i]; c < chunk_ptr[i + 1]; ++c) owner[c] = (int32_t)i;
+}
+__global__ void k_slice_len(const int64_t* rp, int64_t R0, int64_t rows, int64_t nslices,
+                            int32_t* slen, int64_t* sent) {
+  for (int64_t sl = gtid(); sl < nslices; sl += gstride()) {
+    const int64_t r = R0 + 32 * sl;  // rows are sorted by decreasing length
+    const int64_t len = rp[r + 1] - rp[r];
+    slen[sl] = (int32_t)len;
+    sent[sl] = 32 * len;
+  }
+}
+template <class T>
+__global__ void k_fill_sell(const int64_t* rp, const int32_t* col, const double* val, int64_t R0,
+                            int64_t rows, int64_t nslices, const int64_t* sptr,
+                            const int32_t* slen, int32_t* scol, T* sval) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = gtid() >> 5, nwarps = gstride() >> 5;
+  for (int64_t sl = warp; sl < nslices; sl += nwarps) {
+    const int64_t r = R0 + 32 * sl + lane;
+    const int64_t L = slen[sl], base = sptr[sl];
+    int64_t b = 0, len = 0;
+    if (r < rows) {
+      b = rp[r];
+      len = rp[r + 1] - b;
+    }
+    int32_t last = len > 0 ? col[b + len - 1] : 0;
+    for (int64_t k = 0; k < L; ++k) {
+      const bool in = k < len;
+      scol[base + 32 * k + lane] = in ? col[b + k] : last;
+      sval[base + 32 * k + lane] = in ? (T)val[b + k] : (T)0;
+    }
   }
 }
 
 template <class T>
-void build_tiles(DeviceArena& arena, Mat<T>& M, cudaStream_t s) {
-  M.ntiles = 0;
-  M.nlong = 0;
-  M.nchunks = 0;
-  if (M.rows == 0) {
-    M.tile_row = arena.alloc<int32_t>(1);
-    return;
-  }
-  int64_t last_start = 0;
-  PDLP_CUDA_CHECK(cudaMemcpyAsync(&last_start, M.row_ptr + (M.rows - 1), sizeof(int64_t),
-                                  cudaMemcpyDeviceToHost, s));
-  PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
-  const int64_t ntiles = (kUnitRowWeight * (M.rows - 1) + last_start) / kUnitDiag + 1;
-  if (ntiles > INT32_MAX - 1) throw PdlpError(-1, "matrix too large for the row tiling");
-  M.ntiles = (int32_t)ntiles;
-  M.tile_row = arena.alloc<int32_t>(ntiles + 1);
-  k_tile_rows<<<grid_for(ntiles + 1), kThreads, 0, s>>>(M.row_ptr, M.rows, ntiles, M.tile_row);
-  PDLP_LAUNCH_CHECK();
-
-  int64_t* flag = arena.alloc<int64_t>(M.rows);
-  int64_t* pos = arena.alloc<int64_t>(M.rows + 1);
-  int64_t* nch = arena.alloc<int64_t>(M.rows);
-  int64_t* nch_pos = arena.alloc<int64_t>(M.rows + 1);
-  k_long_flags<<<grid_for(M.rows), kThreads, 0, s>>>(M.row_ptr, M.rows, flag, nch);
-  PDLP_LAUNCH_CHECK();
-  exclusive_scan_i64(arena, flag, pos, M.rows, s);
-  exclusive_scan_i64(arena, nch, nch_pos, M.rows, s);
-  int64_t totals[2] = {0, 0};
-  PDLP_CUDA_CHECK(cudaMemcpyAsync(&totals[0], pos + M.rows, sizeof(int64_t),
-                                  cudaMemcpyDeviceToHost, s));
-  PDLP_CUDA_CHECK(cudaMemcpyAsync(&totals[1], nch_pos + M.rows, sizeof(int64_t),
-                                  cudaMemcpyDeviceToHost, s));
-  PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
-  M.nlong = (int32_t)totals[0];
-  M.nchunks = totals[1];
-  M.long_rows = arena.alloc<int32_t>(M.nlong);
-  M.chunk_ptr = arena.alloc<int64_t>(M.nlong + 1);
-  M.chunk_owner = arena.alloc<int32_t>(M.nchunks);
-  M.long_cnt = arena.alloc<unsigned int>(M.nlong);
-  M.long_part = arena.alloc<double>(M.nchunks);
-  M.long_contrib = arena.alloc<double>(2 * (int64_t)M.nlong);
-  PDLP_CUDA_CHECK(cudaMemsetAsync(M.long_cnt, 0, sizeof(unsigned int) * std::max(1, M.nlong), s));
-  PDLP_CUDA_CHECK(cudaMemsetAsync(M.long_contrib, 0, sizeof(double) * 2 * std::max(1, M.nlong), s));
-  if (M.nlong > 0) {
-    k_long_compact<<<grid_for(M.rows), kThreads, 0, s>>>(flag, pos, nch, nch_pos, M.rows,
-                                                         M.long_rows, M.chunk_ptr,
-                                                         M.chunk_owner);
+void build_sell(DeviceArena& arena, Mat<T>& M, const double* val64, cudaStream_t s) {
+  const int64_t rows = M.rows;
+  // long rows: a prefix of the length-sorted rows, rounded up to whole slices
+  unsigned long long* cnt = arena.alloc<unsigned long long>(1);
+  PDLP_CUDA_CHECK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
+  if (rows) {
+    k_count_long<<<grid_for(rows), kThreads, 0, s>>>(M.row_ptr, rows, cnt);
     PDLP_LAUNCH_CHECK();
   }
-  PDLP_CUDA_CHECK(cudaMemcpyAsync(M.chunk_ptr + M.nlong, &M.nchunks, sizeof(int64_t),
-                                  cudaMemcpyHostToDevice, s));
+  unsigned long long nlong = 0;
+  PDLP_CUDA_CHECK(cudaMemcpyAsync(&nlong, cnt, sizeof(nlong), cudaMemcpyDeviceToHost, s));
   PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+  const int64_t R0 = nlong ? std::min<int64_t>(rows, ((int64_t)nlong + 31) / 32 * 32) : 0;
+  M.R0 = (int32_t)R0;
+  M.chunk_ptr = arena.alloc<int64_t>(R0 + 1);
+  int64_t* nch = arena.alloc<int64_t>(R0);
+  if (R0) {
+    k_chunk_counts<<<grid_for(R0), kThreads, 0, s>>>(M.row_ptr, R0, nch);
+    PDLP_LAUNCH_CHECK();
+  }
+  exclusive_scan_i64(arena, nch, M.chunk_ptr, R0, s);
+  PDLP_CUDA_CHECK(cudaMemcpyAsync(&M.nchunks, M.chunk_ptr + R0, sizeof(int64_t),
+                                  cudaMemcpyDeviceToHost, s));
+  PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+  M.chunk_owner = arena.alloc<int32_t>(M.nchunks);
+  if (R0) {
+    k_chunk_owner<<<grid_for(R0), kThreads, 0, s>>>(M.chunk_ptr, R0, M.chunk_owner);
+    PDLP_LAUNCH_CHECK();
+  }
+  M.long_cnt = arena.alloc<unsigned int>(R0);
+  M.long_part = arena.alloc<double>(M.nchunks);
+  M.long_contrib = arena.alloc<double>(2 * R0);
+  PDLP_CUDA_CHECK(cudaMemsetAsync(M.long_cnt, 0, sizeof(unsigned int) * std::max<int64_t>(1, R0), s));
+  PDLP_CUDA_CHECK(cudaMemsetAsync(M.long_contrib, 0, sizeof(double) * 2 * std::max<int64_t>(1, R0), s));
+
+  // SELL-32 of the remaining rows
+  M.nslices = (rows - R0 + 31) / 32;
+  M.slice_ptr = arena.alloc<int64_t>(M.nslices + 1);
+  M.slice_len = arena.alloc<int32_t>(M.nslices);
+  int64_t* sent = arena.alloc<int64_t>(M.nslices);
+  if (M.nslices) {
+    k_slice_len<<<grid_for(M.nslices), kThreads, 0, s>>>(M.row_ptr, R0, rows, M.nslices,
+                                                         M.slice_len, sent);
+    PDLP_LAUNCH_CHECK();
+  }
+  exclusive_scan_i64(arena, sent, M.slice_ptr, M.nslices, s);
+  PDLP_CUDA_CHECK(cudaMemcpyAsync(&M.sell_entries, M.slice_ptr + M.nslices, sizeof(int64_t),
+                                  cudaMemcpyDeviceToHost, s));
+  PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+  M.sell_col = arena.alloc<int32_t>(M.sell_entries);
+  M.sell_val = arena.alloc<T>(M.sell_entries);
+  if (M.nslices) {
+    k_fill_sell<T><<<grid_for(M.nslices * 32), kThreads, 0, s>>>(
+        M.row_ptr, M.col, val64, R0, rows, M.nslices, M.slice_ptr, M.slice_len, M.sell_col,
+        M.sell_val);
+    PDLP_LAUNCH_CHECK();
+  }
 }
 
 template <class T>
@@ -547,8 +660,8 @@ void convert_values(const double* src, T* dst, int64_t len, cudaStream_t s) {
   PDLP_LAUNCH_CHECK();
 }
 
-template void build_tiles<double>(DeviceArena&, Mat<double>&, cudaStream_t);
-template void build_tiles<float>(DeviceArena&, Mat<float>&, cudaStream_t);
+template void build_sell<double>(DeviceArena&, Mat<double>&, const double*, cudaStream_t);
+template void build_sell<float>(DeviceArena&, Mat<float>&, const double*, cudaStream_t);
 template void convert_values<double>(const double*, double*, int64_t, cudaStream_t);
 template void convert_values<float>(const double*, float*, int64_t, cudaStream_t);
 

@@ -35,22 +35,35 @@ static unsigned vec_grid(int64_t len) {
 // ---------------------------------------------------------------------------
 // small vector kernels of the driver
 // ---------------------------------------------------------------------------
-// Preconditioned vectors (Sec. 3): c~ = D2 c, (lc~, uc~) = D1 (lc, uc), (lv~, uv~) = D2^-1 (lv, uv)
+// Preconditioned vectors (Sec. 3): c~ = D2 c, (lc~, uc~) = D1 (lc, uc), (lv~, uv~) = D2^-1 (lv, uv),
+// gathered into the renumbered order (column j' is original column perm_c[j'], row i' is
+// original row perm_r[i']); the unscaled vectors and the scalings are gathered too.
 template <class T>
-__global__ void k_scale_vectors(const double* c, const double* lc, const double* uc,
-                                const double* lv, const double* uv, const double* d1,
-                                const double* d2, int64_t m, int64_t n, T* sc, T* slc, T* suc,
-                                T* slv, T* suv, double* inv_d1, double* inv_d2) {
-  for (int64_t j = sgi(); j < n; j += sgs()) {
-    sc[j] = (T)(d2[j] * c[j]);
-    slv[j] = (T)(lv[j] / d2[j]);
-    suv[j] = (T)(uv[j] / d2[j]);
-    inv_d2[j] = 1.0 / d2[j];
+__global__ void k_prep_vectors(const double* c, const double* lc, const double* uc,
+                               const double* lv, const double* uv, const double* d1,
+                               const double* d2, const int32_t* perm_r, const int32_t* perm_c,
+                               int64_t m, int64_t n, T* sc, T* slc, T* suc, T* slv, T* suv,
+                               double* oc, double* olc, double* ouc, double* olv, double* ouv,
+                               double* d1p, double* d2p, double* inv_d1, double* inv_d2) {
+  for (int64_t jp = sgi(); jp < n; jp += sgs()) {
+    const int64_t j = perm_c ? perm_c[jp] : jp;
+    sc[jp] = (T)(d2[j] * c[j]);
+    slv[jp] = (T)(lv[j] / d2[j]);
+    suv[jp] = (T)(uv[j] / d2[j]);
+    oc[jp] = c[j];
+    olv[jp] = lv[j];
+    ouv[jp] = uv[j];
+    d2p[jp] = d2[j];
+    inv_d2[jp] = 1.0 / d2[j];
   }
-  for (int64_t i = sgi(); i < m; i += sgs()) {
-    slc[i] = (T)(d1[i] * lc[i]);
-    suc[i] = (T)(d1[i] * uc[i]);
-    inv_d1[i] = 1.0 / d1[i];
+  for (int64_t ip = sgi(); ip < m; ip += sgs()) {
+    const int64_t i = perm_r ? perm_r[ip] : ip;
+    slc[ip] = (T)(d1[i] * lc[i]);
+    suc[ip] = (T)(d1[i] * uc[i]);
+    olc[ip] = lc[i];
+    ouc[ip] = uc[i];
+    d1p[ip] = d1[i];
+    inv_d1[ip] = 1.0 / d1[i];
   }
 }
 
@@ -122,13 +135,15 @@ __global__ void k_copy2(const T* a, T* a_out, int64_t na, const T* b, T* b_out, 
   for (int64_t i = sgi(); i < nb; i += sgs()) b_out[i] = b[i];
 }
 
-// x = D2 x~ (kept inside [lv, uv] against the rounding of the product), y = D1 y~
+// x = D2 x~ (kept inside [lv, uv] against the rounding of the product), y = D1 y~,
+// scattered back to the caller's numbering
 template <class T>
 __global__ void k_unscale(const T* x, const T* y, const double* d1, const double* d2,
-                          const double* lv, const double* uv, double* xo, double* yo, int64_t m,
-                          int64_t n) {
-  for (int64_t j = sgi(); j < n; j += sgs()) xo[j] = fmin(fmax(d2[j] * (double)x[j], lv[j]), uv[j]);
-  for (int64_t i = sgi(); i < m; i += sgs()) yo[i] = d1[i] * (double)y[i];
+                          const double* lv, const double* uv, const int32_t* perm_r,
+                          const int32_t* perm_c, double* xo, double* yo, int64_t m, int64_t n) {
+  for (int64_t j = sgi(); j < n; j += sgs())
+    xo[perm_c[j]] = fmin(fmax(d2[j] * (double)x[j], lv[j]), uv[j]);
+  for (int64_t i = sgi(); i < m; i += sgs()) yo[perm_r[i]] = d1[i] * (double)y[i];
 }
 
 template <class T>
@@ -238,7 +253,8 @@ struct Problem {
   double* valT64 = nullptr;  // A~' values in FP64
   double *d1 = nullptr, *d2 = nullptr, *inv_d1 = nullptr, *inv_d2 = nullptr;
   T *c = nullptr, *lc = nullptr, *uc = nullptr, *lv = nullptr, *uv = nullptr;  // scaled
-  DevInputs orig;
+  DevInputs orig;  // unscaled vectors (renumbered when renumber = true)
+  int32_t *perm_r = nullptr, *inv_r = nullptr, *perm_c = nullptr, *inv_c = nullptr;
   double max_abs = 0.0;
   double c_norm = 0.0, b_norm = 0.0;          // ||c||, ||Combine(lc,uc)|| of the unscaled LP
   double c_norm_s = 0.0, b_norm_s = 0.0;      // same for the scaled LP
@@ -261,7 +277,8 @@ static void norms2(Problem<T>& P, const V* c, const V* lc, const V* uc, double* 
 
 template <class T>
 static void build_problem(DeviceArena& arena, const Inputs& in, const DevInputs& d,
-                          int ruiz_iters, double pc_alpha, Problem<T>& P, cudaStream_t s) {
+                          int ruiz_iters, double pc_alpha, Problem<T>& P, cudaStream_t s,
+                          bool renumber = true) {
   P.m = in.m;
   P.n = in.n;
   P.nnz = in.nnz;
@@ -314,32 +331,70 @@ static void build_problem(DeviceArena& arena, const Inputs& in, const DevInputs&
   }
   P.max_abs = max_abs(arena, P.val64, nnz, s);
 
-  // matrix values in the bulk precision
+  if (!renumber) return;  // the preconditioner alone (original numbering)
+
+  // renumber rows and columns by decreasing length, then the SELL-32 / long-row layout
+  P.perm_r = arena.alloc<int32_t>(m);
+  P.inv_r = arena.alloc<int32_t>(m);
+  P.perm_c = arena.alloc<int32_t>(n);
+  P.inv_c = arena.alloc<int32_t>(n);
+  sort_by_length_desc(arena, P.A.row_ptr, m, P.perm_r, P.inv_r, s);
+  sort_by_length_desc(arena, P.AT.row_ptr, n, P.perm_c, P.inv_c, s);
+  Mat<T> A2, AT2;
+  A2.rows = m;
+  A2.cols = n;
+  A2.nnz = nnz;
+  AT2.rows = n;
+  AT2.cols = m;
+  AT2.nnz = nnz;
+  A2.row_ptr = arena.alloc<int64_t>(m + 1);
+  A2.col = arena.alloc<int32_t>(nnz);
+  double* aval = arena.alloc<double>(nnz);
+  AT2.row_ptr = arena.alloc<int64_t>(n + 1);
+  AT2.col = arena.alloc<int32_t>(nnz);
+  double* atval = arena.alloc<double>(nnz);
+  permute_csr(arena, P.A.row_ptr, P.A.col, P.val64, m, P.perm_r, P.inv_c, A2.row_ptr, A2.col,
+              aval, s);
+  permute_csr(arena, P.AT.row_ptr, P.AT.col, P.valT64, n, P.perm_c, P.inv_r, AT2.row_ptr,
+              AT2.col, atval, s);
   if (sizeof(T) == sizeof(double)) {
-    P.A.val = reinterpret_cast<T*>(P.val64);
-    P.AT.val = reinterpret_cast<T*>(P.valT64);
+    A2.val = reinterpret_cast<T*>(aval);
+    AT2.val = reinterpret_cast<T*>(atval);
   } else {
-    P.A.val = arena.alloc<T>(nnz);
-    P.AT.val = arena.alloc<T>(nnz);
-    convert_values<T>(P.val64, P.A.val, nnz, s);
-    convert_values<T>(P.valT64, P.AT.val, nnz, s);
+    A2.val = arena.alloc<T>(nnz);
+    AT2.val = arena.alloc<T>(nnz);
+    convert_values<T>(aval, A2.val, nnz, s);
+    convert_values<T>(atval, AT2.val, nnz, s);
   }
-  build_tiles<T>(arena, P.A, s);
-  build_tiles<T>(arena, P.AT, s);
+  build_sell<T>(arena, A2, aval, s);
+  build_sell<T>(arena, AT2, atval, s);
+  P.A = A2;
+  P.AT = AT2;
 
   P.c = arena.alloc<T>(n);
   P.lv = arena.alloc<T>(n);
   P.uv = arena.alloc<T>(n);
   P.lc = arena.alloc<T>(m);
   P.uc = arena.alloc<T>(m);
+  DevInputs o = d;
+  o.c = arena.alloc<double>(n);
+  o.lv = arena.alloc<double>(n);
+  o.uv = arena.alloc<double>(n);
+  o.lc = arena.alloc<double>(m);
+  o.uc = arena.alloc<double>(m);
+  double* d1p = arena.alloc<double>(m);
+  double* d2p = arena.alloc<double>(n);
   P.inv_d1 = arena.alloc<double>(m);
   P.inv_d2 = arena.alloc<double>(n);
-  k_scale_vectors<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(
-      d.c, d.lc, d.uc, d.lv, d.uv, P.d1, P.d2, m, n, P.c, P.lc, P.uc, P.lv, P.uv, P.inv_d1,
-      P.inv_d2);
+  k_prep_vectors<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(
+      d.c, d.lc, d.uc, d.lv, d.uv, P.d1, P.d2, P.perm_r, P.perm_c, m, n, P.c, P.lc, P.uc, P.lv,
+      P.uv, o.c, o.lc, o.uc, o.lv, o.uv, d1p, d2p, P.inv_d1, P.inv_d2);
   PDLP_LAUNCH_CHECK();
+  P.orig = o;
+  P.d1 = d1p;
+  P.d2 = d2p;
   double o2[2];
-  norms2<double, T>(P, d.c, d.lc, d.uc, o2, s);
+  norms2<double, T>(P, o.c, o.lc, o.uc, o2, s);
   P.c_norm = std::sqrt(o2[0]);
   P.b_norm = std::sqrt(o2[1]);
   norms2<T, T>(P, P.c, P.lc, P.uc, o2, s);
@@ -606,6 +661,14 @@ struct Solver {
     const int64_t trace_iters = (prm.trace_out && prm.trace_iters > 0) ? prm.trace_iters : 0;
     const int64_t rec_len = PDLP_TRACE_HEADER + n + m;
     std::vector<T> hx, hy;
+    std::vector<int32_t> hperm_c, hperm_r;
+    if (trace_iters) {
+      hperm_c.resize(n);
+      hperm_r.resize(m);
+      PDLP_CUDA_CHECK(cudaMemcpyAsync(hperm_c.data(), P.perm_c, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+      if (m) PDLP_CUDA_CHECK(cudaMemcpyAsync(hperm_r.data(), P.perm_r, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s));
+      PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+    }
 
     int status = -100;
     int64_t restarts[3] = {0, 0, 0};
@@ -651,8 +714,8 @@ struct Solver {
           PDLP_CUDA_CHECK(cudaMemcpyAsync(hx.data(), b.X[hs.cur], sizeof(T) * n, cudaMemcpyDeviceToHost, s));
           if (m) PDLP_CUDA_CHECK(cudaMemcpyAsync(hy.data(), b.Y[hs.cur], sizeof(T) * m, cudaMemcpyDeviceToHost, s));
           PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
-          for (int64_t j = 0; j < n; ++j) rec[PDLP_TRACE_HEADER + j] = (double)hx[j];
-          for (int64_t i = 0; i < m; ++i) rec[PDLP_TRACE_HEADER + n + i] = (double)hy[i];
+          for (int64_t j = 0; j < n; ++j) rec[PDLP_TRACE_HEADER + hperm_c[j]] = (double)hx[j];
+          for (int64_t i = 0; i < m; ++i) rec[PDLP_TRACE_HEADER + n + hperm_r[i]] = (double)hy[i];
         }
         if (hs.k > k) attempts_at_last = hs.attempts;
         k = hs.k;
@@ -758,8 +821,8 @@ struct Solver {
       xo = dx_out;
       yo = dy_out;
     }
-    k_unscale<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(out_pt.x, out_pt.y, P.d1, P.d2,
-                                                               P.orig.lv, P.orig.uv, xo, yo, m, n);
+    k_unscale<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(
+        out_pt.x, out_pt.y, P.d1, P.d2, P.orig.lv, P.orig.uv, P.perm_r, P.perm_c, xo, yo, m, n);
     PDLP_LAUNCH_CHECK();
     launches++;
     if (!in.on_device) {
@@ -963,7 +1026,7 @@ int pdlp_precondition(int64_t m, int64_t n, const pdlp_csr* A, const pdlp_params
     copy_in(d.uc, zm.data(), sizeof(double) * m, false, s);
     validate(arena, mat, d, s);
     Problem<double> P;
-    build_problem<double>(arena, mat, d, prm.ruiz_iters, prm.pc_alpha, P, s);
+    build_problem<double>(arena, mat, d, prm.ruiz_iters, prm.pc_alpha, P, s, false);
     const cudaMemcpyKind k = in.on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (d1_out && m) PDLP_CUDA_CHECK(cudaMemcpyAsync(d1_out, P.d1, sizeof(double) * m, k, s));
     if (d2_out) PDLP_CUDA_CHECK(cudaMemcpyAsync(d2_out, P.d2, sizeof(double) * n, k, s));
@@ -991,18 +1054,21 @@ static void stage_point_problem(PointProblem& pp, const Inputs& in, const double
   validate(pp.arena, in, d, s);
   build_problem<double>(pp.arena, in, d, 0, 0.0, pp.P, s);
   const int64_t m = in.m, n = in.n;
-  pp.x = pp.arena.alloc<double>(n);
-  pp.y = pp.arena.alloc<double>(m);
+  auto stage = [&](const double* src, int64_t len, const int32_t* perm) {
+    double* tmp = pp.arena.alloc<double>(len);
+    double* out = pp.arena.alloc<double>(len);
+    copy_in(tmp, src, sizeof(double) * len, in.on_device, s);
+    gather_f64(tmp, perm, out, len, s);
+    return out;
+  };
+  pp.x = stage(x, n, pp.P.perm_c);
+  pp.y = stage(y, m, pp.P.perm_r);
   pp.ax = pp.arena.alloc<double>(m);
   pp.aty = pp.arena.alloc<double>(n);
-  copy_in(pp.x, x, sizeof(double) * n, in.on_device, s);
-  copy_in(pp.y, y, sizeof(double) * m, in.on_device, s);
   pp.xr = pp.yr = nullptr;
   if (xr) {
-    pp.xr = pp.arena.alloc<double>(n);
-    pp.yr = pp.arena.alloc<double>(m);
-    copy_in(pp.xr, xr, sizeof(double) * n, in.on_device, s);
-    copy_in(pp.yr, yr, sizeof(double) * m, in.on_device, s);
+    pp.xr = stage(xr, n, pp.P.perm_c);
+    pp.yr = stage(yr, m, pp.P.perm_r);
   }
   launch_spmv_plain<double>(pp.P.A, pp.x, pp.ax, spmv_grid<double>(pp.P.A, kEpiPlain), s);
   if (m)
