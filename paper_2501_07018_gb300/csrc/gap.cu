@@ -205,6 +205,9 @@ struct GapCtx {
 };
 
 size_t gap_ctx_bytes() { return sizeof(GapCtx); }
+size_t gap_param_bytes(int64_t m, int64_t n) {
+  return sizeof(float4) * (size_t)m + 3 * sizeof(float) * (size_t)n + 256;
+}
 
 // Path of one column: g = c - A'y; it moves toward lv (g > 0) or uv (g < 0) at rate
 // |g| / omega per unit s and parks after travelling `room`.
@@ -274,10 +277,11 @@ __device__ __forceinline__ YPath y_path(double y, double lc, double uc, double a
 }
 
 // Coefficients (alpha, gamma, beta, phi) of a column / row at s.
-__device__ __forceinline__ void x_coef(const XPath& p, double s, double om, double* c4) {
+__device__ __forceinline__ void x_coef(const XPath& p, double s, double om, double iom,
+                                       double* c4) {
   if (!p.moves) return;
   if (s * p.ga < om * p.room) {
-    const double w = p.g * p.g / om;
+    const double w = p.g * p.g * iom;
     c4[0] += w;
     c4[2] += w;
   } else {
@@ -293,7 +297,8 @@ __device__ __forceinline__ int y_piece(const YPath& p, double s, double om) {
   if (p.kind == 3 && s * (om * fabs(p.k2)) >= ay) return 3;
   return 2;
 }
-__device__ __forceinline__ void y_coef(const YPath& p, double s, double om, double* c4) {
+__device__ __forceinline__ void y_coef(const YPath& p, double s, double om, double iom,
+                                       double* c4) {
   if (p.kind == 0) return;
   const int pc = y_piece(p, s, om);
   if (pc == 1) {
@@ -301,7 +306,7 @@ __device__ __forceinline__ void y_coef(const YPath& p, double s, double om, doub
     c4[0] += w;
     c4[2] += w;
   } else if (pc == 2) {
-    c4[1] += p.y * p.y / om;
+    c4[1] += p.y * p.y * iom;
     c4[3] += -p.k1 * p.y;
   } else {
     const double w = om * p.k2 * p.k2;
@@ -310,6 +315,17 @@ __device__ __forceinline__ void y_coef(const YPath& p, double s, double om, doub
     c4[3] += (p.k2 - p.k1) * p.y;
   }
 }
+
+// FP32 parameters of the bracket scan, written by pass 0: per column
+// (|g|, omega room, omega room^2) with |g| = 0 for a column that does not move; per
+// row (omega |k1|, omega |k2|, |y|, y^2 / omega) with omega |k1| = 0 for a fixed row,
+// |y| = +inf for a row that moves away forever and omega |k2| = 0 without a third piece.
+struct ScanParams {
+  float4* row;   // [m]
+  float* xg;     // [n]
+  float* xorm;   // [n]
+  float* xsat;   // [n]
+};
 
 template <class T>
 struct GapArgs {
@@ -321,40 +337,52 @@ struct GapArgs {
   double* part;
   unsigned int* counter;
   int64_t* cand;
+  ScanParams sp;
 };
 
-// pass 0: r^2, slope^2 at 0+, saturated limits, unbounded count
+// pass 0: r^2, slope^2 at 0+, saturated limits, unbounded count; FP32 scan parameters
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_gap_pass0(GapArgs<T> a, double omega) {
   __shared__ double red[5 * kWarps];
   double v[5] = {0, 0, 0, 0, 0};  // r2, slope2, dinf2, finf, unb
-  const double om = omega;
+  const double om = omega, iom = 1.0 / omega;
   for (int64_t j = gi(); j < a.p.n; j += gs()) {
     const double x = a.z.x[j];
     const double dx = x - (double)a.x_ref[j];
     v[0] += om * dx * dx;
     const XPath q = x_path(x, a.p.c[j], a.z.aty[j], a.p.lv[j], a.p.uv[j]);
+    const double orm = om * q.room;
+    a.sp.xg[j] = q.moves ? (float)q.ga : 0.0f;
+    a.sp.xorm[j] = (float)orm;
+    a.sp.xsat[j] = (float)(orm * q.room);
     if (!q.moves) continue;
     if (isinf(q.room)) {
       v[4] += 1.0;
       continue;
     }
-    if (q.room > 0.0) v[1] += q.g * q.g / om;
-    v[2] += om * q.room * q.room;
+    if (q.room > 0.0) v[1] += q.g * q.g * iom;
+    v[2] += orm * q.room;
     v[3] += q.ga * q.room;
   }
   for (int64_t i = gi(); i < a.p.m; i += gs()) {
     const double y = a.z.y[i];
     const double dy = y - (double)a.y_ref[i];
-    v[0] += dy * dy / om;
+    v[0] += dy * dy * iom;
     const YPath q = y_path(y, a.p.lc[i], a.p.uc[i], a.z.ax[i]);
+    const double y2 = q.y * q.y * iom;
+    float4 prm;
+    prm.x = q.kind == 0 ? 0.0f : (float)(om * fabs(q.k1));
+    prm.y = q.kind == 3 ? (float)(om * fabs(q.k2)) : 0.0f;
+    prm.z = q.kind == 1 ? INFINITY : (float)fabs(q.y);
+    prm.w = (float)y2;
+    a.sp.row[i] = prm;
     if (q.kind == 0) continue;
     v[1] += om * q.k1 * q.k1;
     if (q.kind == 1 || q.kind == 3) {
       v[4] += 1.0;
       continue;
     }
-    v[2] += q.y * q.y / om;
+    v[2] += y2;
     v[3] += -q.k1 * q.y;
   }
   block_sum<5>(v, red);
@@ -393,76 +421,10 @@ __global__ void __launch_bounds__(kThreads) k_gap_pass0(GapArgs<T> a, double ome
   }
 }
 
-// squared distance at kGapQ points, accumulated in Acc
-template <class T, class Acc>
-__global__ void __launch_bounds__(kThreads) k_gap_scan(GapArgs<T> a, int plan, int widen) {
-  __shared__ double red[kGapQ * kWarps];
-  __shared__ double s_pts[kGapQ];
-  GapCtx* c = a.ctx;
-  if (c->state != kGapActive || c->plan != plan) return;
-  const double om = c->omega;
-  if (threadIdx.x < kGapQ) {
-    const int q = threadIdx.x;
-    s_pts[q] = (plan == kPlanGeo) ? ldexp(c->s_base, q)
-                                  : c->s_lo + (c->s_hi - c->s_lo) * (double)(q + 1) / (double)(kGapQ + 1);
-  }
-  __syncthreads();
-  Acc pts[kGapQ];
-#pragma unroll
-  for (int q = 0; q < kGapQ; ++q) pts[q] = (Acc)s_pts[q];
-  Acc acc[kGapQ];
-#pragma unroll
-  for (int q = 0; q < kGapQ; ++q) acc[q] = (Acc)0;
-  const Acc omA = (Acc)om, iomA = (Acc)(1.0 / om);
-  for (int64_t j = gi(); j < a.p.n; j += gs()) {
-    // g and the room to the bound in FP64 (both cancel near an optimum), then Acc
-    const double x = a.z.x[j];
-    const double g = (double)a.p.c[j] - (double)a.z.aty[j];
-    if (g == 0.0) continue;
-    const double room = g > 0.0 ? x - (double)a.p.lv[j] : (double)a.p.uv[j] - x;
-    const Acc ga = (Acc)fabs(g);
-    const Acc orm = (Acc)(om * room);
-    const Acc sat = (Acc)(om * room * room);
-#pragma unroll
-    for (int q = 0; q < kGapQ; ++q) {
-      const Acc t = pts[q] * ga;
-      acc[q] += (t < orm) ? t * t * iomA : sat;
-    }
-  }
-  for (int64_t i = gi(); i < a.p.m; i += gs()) {
-    const YPath q0 = y_path((double)a.z.y[i], (double)a.p.lc[i], (double)a.p.uc[i],
-                            (double)a.z.ax[i]);
-    if (q0.kind == 0) continue;
-    const Acc w1 = omA * (Acc)fabs(q0.k1), w2 = omA * (Acc)fabs(q0.k2);
-    const Acc ay = (Acc)fabs(q0.y), y2 = (Acc)(q0.y * q0.y) * iomA;
-    const int kind = q0.kind;
-#pragma unroll
-    for (int q = 0; q < kGapQ; ++q) {
-      const Acc t1 = pts[q] * w1;
-      Acc v;
-      if (kind == 1 || t1 < ay) {
-        v = t1 * t1 * iomA;
-      } else {
-        const Acc t2 = pts[q] * w2;
-        v = (kind == 3 && t2 >= ay) ? t2 * t2 * iomA : y2;
-      }
-      acc[q] += v;
-    }
-  }
-  double v[kGapQ];
-#pragma unroll
-  for (int q = 0; q < kGapQ; ++q) v[q] = (double)acc[q];
-  block_sum<kGapQ>(v, red);
-  const int G = gridDim.x;
-  if (threadIdx.x == 0)
-    for (int q = 0; q < kGapQ; ++q) a.part[q * G + blockIdx.x] = v[q];
-  if (!last_block_arrival(a.counter)) return;
-  __shared__ double d2[kGapQ];
-  for (int q = 0; q < kGapQ; ++q) {
-    const double t = block_sum_array(a.part + q * G, G, red);
-    if (threadIdx.x == 0) d2[q] = t;
-  }
-  if (threadIdx.x != 0) return;
+// New bracket from the squared distances d2 at the scan points (thread 0 of the last
+// CTA of a scan)
+__device__ void gap_update_bracket(GapCtx* c, const double* d2, const double* s_pts, int plan,
+                                   int widen) {
   int first = -1;
   for (int q = 0; q < kGapQ; ++q)
     if (d2[q] >= c->r2) {
@@ -491,21 +453,145 @@ __global__ void __launch_bounds__(kThreads) k_gap_scan(GapArgs<T> a, int plan, i
   }
 }
 
-// exact FP64 coefficients at s_lo, squared distance at s_hi, breakpoints in (s_lo, s_hi]
+// squared distance at kGapQ points, accumulated in Acc, from the pass-0 parameters
+template <class T, class Acc>
+__global__ void __launch_bounds__(kThreads) k_gap_scan(GapArgs<T> a, int plan, int widen) {
+  __shared__ double red[kGapQ * kWarps];
+  __shared__ double s_pts[kGapQ];
+  GapCtx* c = a.ctx;
+  if (c->state != kGapActive || c->plan != plan) return;
+  const double om = c->omega;
+  if (threadIdx.x < kGapQ) {
+    const int q = threadIdx.x;
+    s_pts[q] = (plan == kPlanGeo) ? ldexp(c->s_base, q)
+                                  : c->s_lo + (c->s_hi - c->s_lo) * (double)(q + 1) / (double)(kGapQ + 1);
+  }
+  __syncthreads();
+  Acc pts[kGapQ];
+#pragma unroll
+  for (int q = 0; q < kGapQ; ++q) pts[q] = (Acc)s_pts[q];
+  Acc acc[kGapQ];
+#pragma unroll
+  for (int q = 0; q < kGapQ; ++q) acc[q] = (Acc)0;
+  const Acc iomA = (Acc)(1.0 / om);
+  for (int64_t j = gi(); j < a.p.n; j += gs()) {
+    const Acc ga = (Acc)a.sp.xg[j];
+    if (ga == (Acc)0) continue;
+    const Acc orm = (Acc)a.sp.xorm[j];
+    const Acc sat = (Acc)a.sp.xsat[j];
+#pragma unroll
+    for (int q = 0; q < kGapQ; ++q) {
+      const Acc t = pts[q] * ga;
+      acc[q] += (t < orm) ? t * t * iomA : sat;
+    }
+  }
+  for (int64_t i = gi(); i < a.p.m; i += gs()) {
+    const float4 prm = a.sp.row[i];
+    if (prm.x == 0.0f) continue;
+    const Acc w1 = (Acc)prm.x, w2 = (Acc)prm.y, ay = (Acc)prm.z, y2 = (Acc)prm.w;
+#pragma unroll
+    for (int q = 0; q < kGapQ; ++q) {
+      const Acc t1 = pts[q] * w1;
+      Acc v;
+      if (t1 < ay) {
+        v = t1 * t1 * iomA;
+      } else {
+        const Acc t2 = pts[q] * w2;
+        v = (w2 > (Acc)0 && t2 >= ay) ? t2 * t2 * iomA : y2;
+      }
+      acc[q] += v;
+    }
+  }
+  double v[kGapQ];
+#pragma unroll
+  for (int q = 0; q < kGapQ; ++q) v[q] = (double)acc[q];
+  block_sum<kGapQ>(v, red);
+  const int G = gridDim.x;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < kGapQ; ++q) a.part[q * G + blockIdx.x] = v[q];
+  if (!last_block_arrival(a.counter)) return;
+  __shared__ double d2[kGapQ];
+  for (int q = 0; q < kGapQ; ++q) {
+    const double t = block_sum_array(a.part + q * G, G, red);
+    if (threadIdx.x == 0) d2[q] = t;
+  }
+  if (threadIdx.x != 0) return;
+  gap_update_bracket(c, d2, s_pts, plan, widen);
+}
+
+// FP64 version of the scan for the fallback path: parameters recomputed in FP64
+// from the vectors, so the bracket it returns is reliable where FP32 is not
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_gap_scan64(GapArgs<T> a, int plan, int widen) {
+  __shared__ double red[kGapQ * kWarps];
+  __shared__ double s_pts[kGapQ];
+  GapCtx* c = a.ctx;
+  if (c->state != kGapActive || c->plan != plan) return;
+  const double om = c->omega, iom = 1.0 / om;
+  if (threadIdx.x < kGapQ) {
+    const int q = threadIdx.x;
+    s_pts[q] = (plan == kPlanGeo) ? ldexp(c->s_base, q)
+                                  : c->s_lo + (c->s_hi - c->s_lo) * (double)(q + 1) / (double)(kGapQ + 1);
+  }
+  __syncthreads();
+  double acc[kGapQ];
+#pragma unroll
+  for (int q = 0; q < kGapQ; ++q) acc[q] = 0.0;
+  for (int64_t j = gi(); j < a.p.n; j += gs()) {
+    const XPath p = x_path(a.z.x[j], a.p.c[j], a.z.aty[j], a.p.lv[j], a.p.uv[j]);
+    if (!p.moves) continue;
+    const double orm = om * p.room, sat = orm * p.room;
+#pragma unroll
+    for (int q = 0; q < kGapQ; ++q) {
+      const double t = s_pts[q] * p.ga;
+      acc[q] += (t < orm) ? t * t * iom : sat;
+    }
+  }
+  for (int64_t i = gi(); i < a.p.m; i += gs()) {
+    const YPath p = y_path(a.z.y[i], a.p.lc[i], a.p.uc[i], a.z.ax[i]);
+    if (p.kind == 0) continue;
+    const double w1 = om * fabs(p.k1), w2 = om * fabs(p.k2), ay = fabs(p.y);
+    const double y2 = p.y * p.y * iom;
+#pragma unroll
+    for (int q = 0; q < kGapQ; ++q) {
+      const double t1 = s_pts[q] * w1;
+      double v;
+      if (p.kind == 1 || t1 < ay) {
+        v = t1 * t1 * iom;
+      } else {
+        const double t2 = s_pts[q] * w2;
+        v = (p.kind == 3 && t2 >= ay) ? t2 * t2 * iom : y2;
+      }
+      acc[q] += v;
+    }
+  }
+  block_sum<kGapQ>(acc, red);
+  const int G = gridDim.x;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < kGapQ; ++q) a.part[q * G + blockIdx.x] = acc[q];
+  if (!last_block_arrival(a.counter)) return;
+  __shared__ double d2[kGapQ];
+  for (int q = 0; q < kGapQ; ++q) {
+    const double t = block_sum_array(a.part + q * G, G, red);
+    if (threadIdx.x == 0) d2[q] = t;
+  }
+  if (threadIdx.x != 0) return;
+  gap_update_bracket(c, d2, s_pts, plan, widen);
+}
+
+// exact FP64 coefficients at s_lo and the breakpoints in (s_lo, s_hi]; the squared
+// distance at s_hi is verified by the finish kernel from these
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_gap_exact(GapArgs<T> a) {
-  __shared__ double red[5 * kWarps];
+  __shared__ double red[4 * kWarps];
   GapCtx* c = a.ctx;
   if (c->state != kGapActive) return;
-  const double om = c->omega, slo = c->s_lo, shi = c->s_hi;
-  double v[5] = {0, 0, 0, 0, 0};  // alpha, gamma, beta, phi at s_lo; d2 at s_hi
+  const double om = c->omega, iom = 1.0 / om, slo = c->s_lo, shi = c->s_hi;
+  double v[4] = {0, 0, 0, 0};  // alpha, gamma, beta, phi at s_lo
   for (int64_t j = gi(); j < a.p.n; j += gs()) {
     const XPath q = x_path(a.z.x[j], a.p.c[j], a.z.aty[j], a.p.lv[j], a.p.uv[j]);
     if (!q.moves) continue;
-    x_coef(q, slo, om, v);
-    double h[4] = {0, 0, 0, 0};
-    x_coef(q, shi, om, h);
-    v[4] += h[0] * shi * shi + h[1];
+    x_coef(q, slo, om, iom, v);
     const double orm = om * q.room;
     if (slo * q.ga < orm && orm <= shi * q.ga) {
       const int k = atomicAdd(&c->ncand, 1);
@@ -515,10 +601,7 @@ __global__ void __launch_bounds__(kThreads) k_gap_exact(GapArgs<T> a) {
   for (int64_t i = gi(); i < a.p.m; i += gs()) {
     const YPath q = y_path(a.z.y[i], a.p.lc[i], a.p.uc[i], a.z.ax[i]);
     if (q.kind == 0) continue;
-    y_coef(q, slo, om, v);
-    double h[4] = {0, 0, 0, 0};
-    y_coef(q, shi, om, h);
-    v[4] += h[0] * shi * shi + h[1];
+    y_coef(q, slo, om, iom, v);
     if (q.kind == 1) continue;
     const double ay = fabs(q.y);
     const double w1 = om * fabs(q.k1);
@@ -534,24 +617,22 @@ __global__ void __launch_bounds__(kThreads) k_gap_exact(GapArgs<T> a) {
       }
     }
   }
-  block_sum<5>(v, red);
+  block_sum<4>(v, red);
   const int G = gridDim.x;
   if (threadIdx.x == 0)
-    for (int k = 0; k < 5; ++k) a.part[k * G + blockIdx.x] = v[k];
+    for (int k = 0; k < 4; ++k) a.part[k * G + blockIdx.x] = v[k];
   if (!last_block_arrival(a.counter)) return;
-  double t[5];
-  for (int k = 0; k < 5; ++k) t[k] = block_sum_array(a.part + k * G, G, red);
+  double t[4];
+  for (int k = 0; k < 4; ++k) t[k] = block_sum_array(a.part + k * G, G, red);
   if (threadIdx.x != 0) return;
   c->alpha = t[0];
   c->gamma = t[1];
   c->beta = t[2];
   c->phi = t[3];
   c->d2lo = t[0] * slo * slo + t[1];
-  c->d2hi = t[4];
   const int nc = ((volatile int*)&c->ncand)[0];
-  // the bracket must contain the crossing (up to rounding of the two summation orders)
-  const bool ok = c->d2lo < c->r2 * (1.0 + 1e-12) && c->d2hi >= c->r2 * (1.0 - 1e-12);
-  if (!ok || nc > kGapCandCap) c->state = kGapFailed;
+  // the crossing must not lie left of the bracket (up to rounding)
+  if (!(c->d2lo < c->r2 * (1.0 + 1e-12)) || nc > kGapCandCap) c->state = kGapFailed;
 }
 
 // breakpoint value and coefficient change of one candidate
@@ -563,7 +644,7 @@ __device__ void cand_info(const GapArgs<T>& a, double om, int64_t code, double* 
   if (which == 0) {
     const XPath q = x_path(a.z.x[idx], a.p.c[idx], a.z.aty[idx], a.p.lv[idx], a.p.uv[idx]);
     *bp = om * q.room / q.ga;
-    const double w = q.g * q.g / om;
+    const double w = q.g * q.g * (1.0 / om);
     d4[0] = -w;
     d4[1] = om * q.room * q.room;
     d4[2] = -w;
@@ -575,14 +656,14 @@ __device__ void cand_info(const GapArgs<T>& a, double om, int64_t code, double* 
       *bp = ay / (om * fabs(q.k1));
       const double w = om * q.k1 * q.k1;
       d4[0] = -w;
-      d4[1] = q.y * q.y / om;
+      d4[1] = q.y * q.y * (1.0 / om);
       d4[2] = -w;
       d4[3] = -q.k1 * q.y;
     } else {
       *bp = ay / (om * fabs(q.k2));
       const double w = om * q.k2 * q.k2;
       d4[0] = w;
-      d4[1] = -q.y * q.y / om;
+      d4[1] = -q.y * q.y * (1.0 / om);
       d4[2] = w;
       d4[3] = q.k2 * q.y;
     }
@@ -693,6 +774,15 @@ __global__ void __launch_bounds__(kThreads) k_gap_finish(GapArgs<T> a) {
     for (int k = 0; k < 4; ++k) s_coef[k] = off[k] + dl[first - owner * kFinPer][k];
   __syncthreads();
   if (tid != 0) return;
+  {
+    // verify the right end of the bracket: alpha(s_hi) s_hi^2 + gamma(s_hi) >= r^2
+    const double a_hi = c->alpha + s_tot[0], g_hi = c->gamma + s_tot[1];
+    c->d2hi = a_hi * c->s_hi * c->s_hi + g_hi;
+    if (first == INT_MAX && !(c->d2hi >= r2 * (1.0 - 1e-12))) {
+      c->state = kGapFailed;
+      return;
+    }
+  }
   double cf[4];
   double lo_b, hi_b;
   if (first == INT_MAX) {
@@ -741,6 +831,14 @@ double normalized_gap(const PointRef<T>& z, const T* x_ref, const T* y_ref, doub
   a.part = gsc.part;
   a.counter = gsc.counter;
   a.cand = gsc.cand;
+  {
+    char* base = static_cast<char*>(gsc.params);
+    a.sp.row = reinterpret_cast<float4*>(base);
+    base += sizeof(float4) * (size_t)p.m;
+    a.sp.xg = reinterpret_cast<float*>(base);
+    a.sp.xorm = a.sp.xg + p.n;
+    a.sp.xsat = a.sp.xorm + p.n;
+  }
   const int G = gsc.grid;
   int nl = 0;
   k_gap_pass0<T><<<G, kThreads, 0, s>>>(a, omega);
@@ -761,7 +859,7 @@ double normalized_gap(const PointRef<T>& z, const T* x_ref, const T* y_ref, doub
     double scale = 1.0;
     for (int rep = 0; rep < 64; ++rep) {
       k_gap_set<<<1, 1, 0, s>>>(gsc.ctx, kGapActive, kPlanGeo, scale);
-      k_gap_scan<T, double><<<G, kThreads, 0, s>>>(a, kPlanGeo, 0);
+      k_gap_scan64<T><<<G, kThreads, 0, s>>>(a, kPlanGeo, 0);
       nl += 2;
       PDLP_LAUNCH_CHECK();
       PDLP_CUDA_CHECK(cudaMemcpyAsync(&h, gsc.ctx, sizeof(GapCtx), cudaMemcpyDeviceToHost, s));
@@ -787,7 +885,7 @@ double normalized_gap(const PointRef<T>& z, const T* x_ref, const T* y_ref, doub
         break;
       }
       k_gap_set<<<1, 1, 0, s>>>(gsc.ctx, kGapActive, kPlanLin, 1.0);
-      k_gap_scan<T, double><<<G, kThreads, 0, s>>>(a, kPlanLin, 1);
+      k_gap_scan64<T><<<G, kThreads, 0, s>>>(a, kPlanLin, 1);
       nl += 2;
       PDLP_LAUNCH_CHECK();
     }

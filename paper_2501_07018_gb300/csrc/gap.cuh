@@ -65,8 +65,10 @@ struct GapScratch {
   double* part;  // [kGapPartials * grid]
   unsigned int* counter;
   int64_t* cand;  // [kGapCandCap] candidate breakpoints
+  void* params;   // gap_param_bytes(m, n): FP32 scan parameters written by pass 0
   int grid;
 };
+size_t gap_param_bytes(int64_t m, int64_t n);
 constexpr int kGapQ = 32;
 constexpr int kGapCandCap = 2048;
 constexpr int kGapPartials = kGapQ + 8;

@@ -66,13 +66,34 @@ __global__ void __launch_bounds__(kThreads) k_primal(IterBuffers<T> b, DevState*
     const T tau = (T)(eta / omega);
     const T* __restrict__ x = b.X[cur];
     const T* __restrict__ aty = b.ATY[cur];
+    const T* __restrict__ c = b.c;
+    const T* __restrict__ lv = b.lv;
+    const T* __restrict__ uv = b.uv;
     T* __restrict__ xn = b.X[cur ^ 1];
-    for (int64_t j = gtid2(); j < b.n; j += gstride2()) {
-      const T xo = x[j];
-      const T v = clampv<T>(xo - tau * (b.c[j] - aty[j]), b.lv[j], b.uv[j]);
-      xn[j] = v;
-      const A d = (A)v - (A)xo;
-      lacc = fma(d, d, lacc);
+    constexpr int U = 4;
+    const int64_t stride = gstride2();
+    for (int64_t j0 = gtid2(); j0 < b.n; j0 += U * stride) {
+      T xo[U], g[U], lo[U], hi[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t j = j0 + u * stride;
+        if (j < b.n) {
+          xo[u] = x[j];
+          g[u] = c[j] - aty[j];
+          lo[u] = lv[j];
+          hi[u] = uv[j];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t j = j0 + u * stride;
+        if (j < b.n) {
+          const T v = clampv<T>(xo[u] - tau * g[u], lo[u], hi[u]);
+          xn[j] = v;
+          const A d = (A)v - (A)xo[u];
+          lacc = fma(d, d, lacc);
+        }
+      }
     }
   }
   double acc[1] = {(double)lacc};
@@ -371,9 +392,9 @@ int spmv_grid(const Mat<T>& M, int epi) {
 }
 
 int primal_grid(int64_t n) {
-  // about two elements per thread: enough independent loads in flight per SM
-  const int64_t need = (n + kThreads * 2 - 1) / (kThreads * 2);
-  return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 64));
+  // resident CTAs only; each thread keeps four elements' loads in flight
+  const int64_t need = (n + kThreads - 1) / kThreads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 8));
 }
 
 template <class T>

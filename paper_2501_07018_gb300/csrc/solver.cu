@@ -546,6 +546,7 @@ struct Solver {
     gsc.part = arena.alloc<double>((int64_t)kGapPartials * g_red);
     gsc.counter = counters + 2;
     gsc.cand = arena.alloc<int64_t>(kGapCandCap);
+    gsc.params = arena.alloc_bytes(gap_param_bytes(m, n));
     dist_part = arena.alloc<double>(2 * (int64_t)g_red);
     dist_out = arena.alloc<double>(2);
   }
@@ -1100,6 +1101,7 @@ int pdlp_normalized_gap(int64_t m, int64_t n, const pdlp_csr* A, const double* c
     gsc.part = pp.arena.alloc<double>((int64_t)kGapPartials * g);
     gsc.counter = pp.arena.alloc<unsigned int>(1);
     gsc.cand = pp.arena.alloc<int64_t>(kGapCandCap);
+    gsc.params = pp.arena.alloc_bytes(gap_param_bytes(m, n));
     PDLP_CUDA_CHECK(cudaMemsetAsync(gsc.counter, 0, sizeof(unsigned int), sg.s));
     const ScaledVecs<double> sv{pp.P.c, pp.P.lc, pp.P.uc, pp.P.lv, pp.P.uv, m, n};
     GapStats gst;
