@@ -43,10 +43,10 @@ CPU_SAMPLE_ITERS = 12
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--iters-per-step", type=int, default=1000)
+    ap.add_argument("--iters-per-step", type=int, default=5000)
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the LP (testing only)")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--cpu-sample-child", action="store_true", help=argparse.SUPPRESS)

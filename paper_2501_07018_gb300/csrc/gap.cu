@@ -698,10 +698,12 @@ __global__ void __launch_bounds__(kThreads) k_gap_finish(GapArgs<T> a) {
     }
   }
   __syncthreads();
-  // bitonic sort by (key, code)
-  for (int k = 2; k <= kGapCandCap; k <<= 1) {
+  // bitonic sort by (key, code) over the smallest power of two holding the candidates
+  int P = 2;
+  while (P < nc) P <<= 1;
+  for (int k = 2; k <= P; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = tid; i < kGapCandCap; i += kThreads) {
+      for (int i = tid; i < P; i += kThreads) {
         const int l = i ^ j;
         if (l > i) {
           const bool up = (i & k) == 0;
