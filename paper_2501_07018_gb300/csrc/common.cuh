@@ -105,6 +105,22 @@ __device__ __forceinline__ double block_sum_array(const double* partials, int co
   return v[0];
 }
 
+// Sums each of K arrays partials[k*count .. k*count+count) by one CTA in a single
+// pass: a group of blockDim/K threads (a power of two <= 32) per array reads it
+// strided, then shuffles; every thread of the group holds the result.  The order is
+// fixed, so the result is deterministic.  Requires blockDim.x % K == 0 and K <= blockDim.x.
+template <int K>
+__device__ __forceinline__ double group_sum_arrays(const double* partials, int count) {
+  constexpr int GS = (kThreads / K) >= 32 ? 32 : (kThreads / K);
+  const int k = threadIdx.x / GS, r = threadIdx.x % GS;
+  double v = 0.0;
+  if (k < K)
+    for (int i = r; i < count; i += GS) v += ((volatile const double*)partials)[k * count + i];
+#pragma unroll
+  for (int o = GS >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, GS);
+  return v;
+}
+
 // ---------------------------------------------------------------------------
 // device-resident scalar state of the PDHG loop (Algorithm 1 / Algorithm 2)
 // ---------------------------------------------------------------------------

@@ -511,10 +511,12 @@ __global__ void __launch_bounds__(kThreads) k_gap_scan(GapArgs<T> a, int plan, i
     for (int q = 0; q < kGapQ; ++q) a.part[q * G + blockIdx.x] = v[q];
   if (!last_block_arrival(a.counter)) return;
   __shared__ double d2[kGapQ];
-  for (int q = 0; q < kGapQ; ++q) {
-    const double t = block_sum_array(a.part + q * G, G, red);
-    if (threadIdx.x == 0) d2[q] = t;
+  {
+    const double t = group_sum_arrays<kGapQ>(a.part, G);
+    constexpr int GS = kThreads / kGapQ;
+    if (threadIdx.x % GS == 0) d2[threadIdx.x / GS] = t;
   }
+  __syncthreads();
   if (threadIdx.x != 0) return;
   gap_update_bracket(c, d2, s_pts, plan, widen);
 }
@@ -571,10 +573,12 @@ __global__ void __launch_bounds__(kThreads) k_gap_scan64(GapArgs<T> a, int plan,
     for (int q = 0; q < kGapQ; ++q) a.part[q * G + blockIdx.x] = acc[q];
   if (!last_block_arrival(a.counter)) return;
   __shared__ double d2[kGapQ];
-  for (int q = 0; q < kGapQ; ++q) {
-    const double t = block_sum_array(a.part + q * G, G, red);
-    if (threadIdx.x == 0) d2[q] = t;
+  {
+    const double t = group_sum_arrays<kGapQ>(a.part, G);
+    constexpr int GS = kThreads / kGapQ;
+    if (threadIdx.x % GS == 0) d2[threadIdx.x / GS] = t;
   }
+  __syncthreads();
   if (threadIdx.x != 0) return;
   gap_update_bracket(c, d2, s_pts, plan, widen);
 }

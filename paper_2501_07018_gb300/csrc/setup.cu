@@ -439,24 +439,42 @@ void gather_f64(const double* in, const int32_t* perm, double* out, int64_t len,
 // ---------------------------------------------------------------------------
 // preconditioning passes
 // ---------------------------------------------------------------------------
+// One group of G lanes per row (G chosen from the mean row length); the loop trip
+// count is uniform across a warp so the group shuffles are safe.
+template <int G>
 __global__ void k_row_norms(const int64_t* rp, const double* val, int64_t rows, int kind,
                             double p, double* out) {
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, lg = lane % G;
+  const int64_t per_warp = 32 / G;
   const int64_t warp = gtid() >> 5, nwarps = gstride() >> 5;
-  for (int64_t i = warp; i < rows; i += nwarps) {
+  for (int64_t i0 = warp * per_warp; i0 < rows; i0 += nwarps * per_warp) {
+    const int64_t i = i0 + lane / G;
     double acc = 0.0;
-    for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += 32) {
-      const double a = fabs(val[e]);
-      if (kind == 0)
-        acc = fmax(acc, a);
-      else if (kind == 1)
-        acc += a;
-      else
-        acc += pow(a, p);
+    if (i < rows) {
+      for (int64_t e = rp[i] + lg; e < rp[i + 1]; e += G) {
+        const double a = fabs(val[e]);
+        if (kind == 0)
+          acc = fmax(acc, a);
+        else if (kind == 1)
+          acc += a;
+        else
+          acc += pow(a, p);
+      }
     }
-    acc = (kind == 0) ? warp_max(acc) : warp_sum(acc);
-    if (lane == 0) out[i] = (kind == 2 && acc > 0.0) ? pow(acc, 1.0 / p) : acc;
+#pragma unroll
+    for (int o = G >> 1; o > 0; o >>= 1) {
+      const double t = __shfl_xor_sync(0xffffffffu, acc, o, G);
+      acc = (kind == 0) ? fmax(acc, t) : acc + t;
+    }
+    if (i < rows && lg == 0) out[i] = (kind == 2 && acc > 0.0) ? pow(acc, 1.0 / p) : acc;
   }
+}
+
+static int group_for(int64_t nnz, int64_t rows) {
+  const double avg = rows > 0 ? (double)nnz / (double)rows : 1.0;
+  int g = 1;
+  while (g < 32 && g < avg) g <<= 1;
+  return g;
 }
 
 __global__ void k_scale_factors(const double* norms, int64_t len, double* f, double* acc) {
@@ -470,15 +488,20 @@ __global__ void k_scale_factors(const double* norms, int64_t len, double* f, dou
 
 // The entry in row `row`, column col[e] becomes (val * f_first[.]) * f_second[.] where
 // f_first is indexed by the column (first_is_col) or the row, f_second by the other.
+// One group of G lanes per row, as in k_row_norms.
+template <int G>
 __global__ void k_scale_values(const int64_t* rp, const int32_t* col, double* val, int64_t rows,
                                const double* f_first, const double* f_second,
                                bool first_is_col) {
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, lg = lane % G;
+  const int64_t per_warp = 32 / G;
   const int64_t warp = gtid() >> 5, nwarps = gstride() >> 5;
-  for (int64_t i = warp; i < rows; i += nwarps) {
+  for (int64_t i0 = warp * per_warp; i0 < rows; i0 += nwarps * per_warp) {
+    const int64_t i = i0 + lane / G;
+    if (i >= rows) continue;
     const double fr = first_is_col ? 0.0 : f_first[i];
     const double fs = first_is_col ? f_second[i] : 0.0;
-    for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += 32) {
+    for (int64_t e = rp[i] + lg; e < rp[i + 1]; e += G) {
       const int32_t j = col[e];
       double v;
       if (first_is_col)
@@ -504,10 +527,27 @@ __global__ void k_max_abs_partial(const double* v, int64_t len, double* part) {
   }
 }
 
+#define PDLP_GROUP_DISPATCH(G, CALL) \
+  switch (G) {                          \
+    case 1: CALL(1); break;             \
+    case 2: CALL(2); break;             \
+    case 4: CALL(4); break;             \
+    case 8: CALL(8); break;             \
+    case 16: CALL(16); break;           \
+    default: CALL(32); break;           \
+  }
+
 void row_norms(const int64_t* rp, const double* val, int64_t rows, int kind, double p,
                double* out, cudaStream_t s) {
   if (rows == 0) return;
-  k_row_norms<<<grid_for(rows * 32), kThreads, 0, s>>>(rp, val, rows, kind, p, out);
+  int64_t nnz = 0;
+  PDLP_CUDA_CHECK(cudaMemcpyAsync(&nnz, rp + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+  const int g = group_for(nnz, rows);
+  const unsigned grid = grid_for((rows * g + 31) / 32 * 32);
+#define PDLP_NORMS(G) k_row_norms<G><<<grid, kThreads, 0, s>>>(rp, val, rows, kind, p, out)
+  PDLP_GROUP_DISPATCH(g, PDLP_NORMS)
+#undef PDLP_NORMS
   PDLP_LAUNCH_CHECK();
 }
 void scale_factors(const double* norms, int64_t len, double* f, double* acc, cudaStream_t s) {
@@ -519,8 +559,15 @@ void scale_values(const int64_t* rp, const int32_t* col, double* val, int64_t ro
                   const double* f_first, const double* f_second, bool first_is_col,
                   cudaStream_t s) {
   if (rows == 0) return;
-  k_scale_values<<<grid_for(rows * 32), kThreads, 0, s>>>(rp, col, val, rows, f_first, f_second,
-                                                          first_is_col);
+  int64_t nnz = 0;
+  PDLP_CUDA_CHECK(cudaMemcpyAsync(&nnz, rp + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+  const int g = group_for(nnz, rows);
+  const unsigned grid = grid_for((rows * g + 31) / 32 * 32);
+#define PDLP_SCALE(G) \
+  k_scale_values<G><<<grid, kThreads, 0, s>>>(rp, col, val, rows, f_first, f_second, first_is_col)
+  PDLP_GROUP_DISPATCH(g, PDLP_SCALE)
+#undef PDLP_SCALE
   PDLP_LAUNCH_CHECK();
 }
 double max_abs(DeviceArena& arena, const double* v, int64_t len, cudaStream_t s) {
