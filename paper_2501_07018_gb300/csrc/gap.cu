@@ -343,61 +343,70 @@ struct GapArgs {
 // pass 0: r^2, slope^2 at 0+, saturated limits, unbounded count; FP32 scan parameters
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_gap_pass0(GapArgs<T> a, double omega) {
-  __shared__ double red[5 * kWarps];
-  double v[5] = {0, 0, 0, 0, 0};  // r2, slope2, dinf2, finf, unb
+  __shared__ double red6[6 * kWarps];
+  // v: sum dx^2, sum dy^2 (r^2 = omega sum dx^2 + sum dy^2 / omega), dinf2, finf; the
+  // slope at 0+ only positions the bracket and is accumulated in FP32
+  double v[5] = {0, 0, 0, 0, 0};
+  float slope = 0.0f;
+  unsigned int unb = 0;
   const double om = omega, iom = 1.0 / omega;
+  const float iomf = (float)iom, omf = (float)om;
   for (int64_t j = gi(); j < a.p.n; j += gs()) {
     const double x = a.z.x[j];
     const double dx = x - (double)a.x_ref[j];
-    v[0] += om * dx * dx;
+    v[0] = fma(dx, dx, v[0]);
     const XPath q = x_path(x, a.p.c[j], a.z.aty[j], a.p.lv[j], a.p.uv[j]);
     const double orm = om * q.room;
-    a.sp.xg[j] = q.moves ? (float)q.ga : 0.0f;
-    a.sp.xorm[j] = (float)orm;
-    a.sp.xsat[j] = (float)(orm * q.room);
+    const float gaf = q.moves ? (float)q.ga : 0.0f, ormf = (float)orm, roomf = (float)q.room;
+    a.sp.xg[j] = gaf;
+    a.sp.xorm[j] = ormf;
+    a.sp.xsat[j] = ormf * roomf;
     if (!q.moves) continue;
     if (isinf(q.room)) {
-      v[4] += 1.0;
+      ++unb;
       continue;
     }
-    if (q.room > 0.0) v[1] += q.g * q.g * iom;
-    v[2] += orm * q.room;
-    v[3] += q.ga * q.room;
+    if (q.room > 0.0) slope = fmaf(gaf * gaf, iomf, slope);
+    v[2] = fma(orm, q.room, v[2]);
+    v[3] = fma(q.ga, q.room, v[3]);
   }
   for (int64_t i = gi(); i < a.p.m; i += gs()) {
     const double y = a.z.y[i];
     const double dy = y - (double)a.y_ref[i];
-    v[0] += dy * dy * iom;
+    v[1] = fma(dy, dy, v[1]);
     const YPath q = y_path(y, a.p.lc[i], a.p.uc[i], a.z.ax[i]);
-    const double y2 = q.y * q.y * iom;
+    const float yf = (float)q.y;
+    const float y2f = yf * yf * iomf;
+    const float w1 = omf * fabsf((float)q.k1);
     float4 prm;
-    prm.x = q.kind == 0 ? 0.0f : (float)(om * fabs(q.k1));
-    prm.y = q.kind == 3 ? (float)(om * fabs(q.k2)) : 0.0f;
-    prm.z = q.kind == 1 ? INFINITY : (float)fabs(q.y);
-    prm.w = (float)y2;
+    prm.x = q.kind == 0 ? 0.0f : w1;
+    prm.y = q.kind == 3 ? omf * fabsf((float)q.k2) : 0.0f;
+    prm.z = q.kind == 1 ? INFINITY : fabsf(yf);
+    prm.w = y2f;
     a.sp.row[i] = prm;
     if (q.kind == 0) continue;
-    v[1] += om * q.k1 * q.k1;
+    slope = fmaf(w1, fabsf((float)q.k1), slope);
     if (q.kind == 1 || q.kind == 3) {
-      v[4] += 1.0;
+      ++unb;
       continue;
     }
-    v[2] += y2;
-    v[3] += -q.k1 * q.y;
+    v[2] = fma(q.y * q.y, iom, v[2]);
+    v[3] = fma(-q.k1, q.y, v[3]);
   }
-  block_sum<5>(v, red);
+  double w6[6] = {v[0], v[1], v[2], v[3], (double)unb, (double)slope};
+  block_sum<6>(w6, red6);
   const int G = gridDim.x;
   if (threadIdx.x == 0)
-    for (int k = 0; k < 5; ++k) a.part[k * G + blockIdx.x] = v[k];
+    for (int k = 0; k < 6; ++k) a.part[k * G + blockIdx.x] = w6[k];
   if (!last_block_arrival(a.counter)) return;
-  double t[5];
-  for (int k = 0; k < 5; ++k) t[k] = block_sum_array(a.part + k * G, G, red);
+  double t[6];
+  for (int k = 0; k < 6; ++k) t[k] = block_sum_array(a.part + k * G, G, red6);
   if (threadIdx.x != 0) return;
   GapCtx* c = a.ctx;
   c->omega = om;
-  c->r2 = t[0];
-  c->r = sqrt(t[0]);
-  c->slope2 = t[1];
+  c->r2 = om * t[0] + t[1] / om;
+  c->r = sqrt(c->r2);
+  c->slope2 = t[5];
   c->dinf2 = t[2];
   c->finf = t[3];
   c->unb = (int)t[4];
@@ -502,13 +511,26 @@ __global__ void __launch_bounds__(kThreads) k_gap_scan(GapArgs<T> a, int plan, i
       acc[q] += v;
     }
   }
-  double v[kGapQ];
+  // warp stage in Acc (a double shuffle tree per value would load the FP64 pipe more
+  // than the scan itself), then one FP64 sum over the warps per value
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int q = 0; q < kGapQ; ++q) v[q] = (double)acc[q];
-  block_sum<kGapQ>(v, red);
+  for (int q = 0; q < kGapQ; ++q) {
+    Acc t = acc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    acc[q] = t;
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < kGapQ; ++q) red[q * kWarps + warp] = (double)acc[q];
+  __syncthreads();
   const int G = gridDim.x;
-  if (threadIdx.x == 0)
-    for (int q = 0; q < kGapQ; ++q) a.part[q * G + blockIdx.x] = v[q];
+  if (threadIdx.x < kGapQ) {
+    double t = 0.0;
+    for (int w = 0; w < kWarps; ++w) t += red[threadIdx.x * kWarps + w];
+    a.part[threadIdx.x * G + blockIdx.x] = t;
+  }
   if (!last_block_arrival(a.counter)) return;
   __shared__ double d2[kGapQ];
   {

@@ -256,7 +256,8 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs<T> a) {
       const int L = M.slice_len[sl];
       const int32_t* __restrict__ cp = M.sell_col + M.slice_ptr[sl] + lane;
       const T* __restrict__ vp = M.sell_val + M.slice_ptr[sl] + lane;
-      T acc = (T)0;
+      // two independent FMA chains (even / odd entries) for instruction-level parallelism
+      T acc_e = (T)0, acc_o = (T)0;
       for (int k0 = 0; k0 < L; k0 += kBatch) {
         int cr[kBatch];
         T vr[kBatch], xr[kBatch];
@@ -269,9 +270,16 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs<T> a) {
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) xr[u] = (k0 + u < L) ? src[cr[u]] : (T)0;
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u)
-          if (k0 + u < L) acc = fma(vr[u], xr[u], acc);
+        for (int u = 0; u < kBatch; ++u) {
+          if (k0 + u < L) {
+            if (u & 1)
+              acc_o = fma(vr[u], xr[u], acc_o);
+            else
+              acc_e = fma(vr[u], xr[u], acc_e);
+          }
+        }
       }
+      const T acc = acc_e + acc_o;
       if (own) row_epilogue<T, EPI, A>(e, ein, row, acc, c0, c1);
     } else {
       // one chunk of a long row (CSR)
