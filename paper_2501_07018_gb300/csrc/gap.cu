@@ -362,11 +362,11 @@ __global__ void __launch_bounds__(kThreads) k_gap_pass0(GapArgs<T> a, double ome
     a.sp.xorm[j] = ormf;
     a.sp.xsat[j] = ormf * roomf;
     if (!q.moves) continue;
+    if (q.room > 0.0) slope = fmaf(gaf * gaf, iomf, slope);  // every column that moves at 0+
     if (isinf(q.room)) {
       ++unb;
       continue;
     }
-    if (q.room > 0.0) slope = fmaf(gaf * gaf, iomf, slope);
     v[2] = fma(orm, q.room, v[2]);
     v[3] = fma(q.ga, q.room, v[3]);
   }
@@ -441,11 +441,18 @@ __device__ void gap_update_bracket(GapCtx* c, const double* d2, const double* s_
       break;
     }
   if (plan == kPlanGeo) {
+    // points s_base * 2^(q - kGapQ/2); a crossing off either end moves the window
     if (first < 0) {
+      c->s_base = ldexp(c->s_base, kGapQ);
       c->state = kGapNeedMore;
       return;
     }
-    c->s_lo = first == 0 ? 0.5 * s_pts[0] : s_pts[first - 1];
+    if (first == 0) {
+      c->s_base = ldexp(c->s_base, -kGapQ);
+      c->state = kGapNeedMore;
+      return;
+    }
+    c->s_lo = s_pts[first - 1];
     c->s_hi = s_pts[first];
     c->plan = kPlanLin;
   } else {
@@ -472,7 +479,7 @@ __global__ void __launch_bounds__(kThreads) k_gap_scan(GapArgs<T> a, int plan, i
   const double om = c->omega;
   if (threadIdx.x < kGapQ) {
     const int q = threadIdx.x;
-    s_pts[q] = (plan == kPlanGeo) ? ldexp(c->s_base, q)
+    s_pts[q] = (plan == kPlanGeo) ? ldexp(c->s_base, q - kGapQ / 2)
                                   : c->s_lo + (c->s_hi - c->s_lo) * (double)(q + 1) / (double)(kGapQ + 1);
   }
   __syncthreads();
@@ -554,7 +561,7 @@ __global__ void __launch_bounds__(kThreads) k_gap_scan64(GapArgs<T> a, int plan,
   const double om = c->omega, iom = 1.0 / om;
   if (threadIdx.x < kGapQ) {
     const int q = threadIdx.x;
-    s_pts[q] = (plan == kPlanGeo) ? ldexp(c->s_base, q)
+    s_pts[q] = (plan == kPlanGeo) ? ldexp(c->s_base, q - kGapQ / 2)
                                   : c->s_lo + (c->s_hi - c->s_lo) * (double)(q + 1) / (double)(kGapQ + 1);
   }
   __syncthreads();
@@ -831,10 +838,11 @@ __global__ void __launch_bounds__(kThreads) k_gap_finish(GapArgs<T> a) {
   c->state = kGapDone;
 }
 
-__global__ void k_gap_set(GapCtx* c, int state, int plan, double base_scale) {
+// reset_base: restart the geometric window at the lower-bound estimate
+__global__ void k_gap_set(GapCtx* c, int state, int plan, int reset_base) {
   c->state = state;
   c->plan = plan;
-  if (plan == kPlanGeo) c->s_base = c->s_lb * base_scale;
+  if (reset_base) c->s_base = c->s_lb;
   c->ncand = 0;
 }
 __global__ void k_gap_clear_cand(GapCtx* c) { c->ncand = 0; }
@@ -882,18 +890,17 @@ double normalized_gap(const PointRef<T>& z, const T* x_ref, const T* y_ref, doub
   PDLP_CUDA_CHECK(cudaMemcpyAsync(&h, gsc.ctx, sizeof(GapCtx), cudaMemcpyDeviceToHost, s));
   PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
   if (h.state != kGapDone) {
-    // FP64 scan from the lower bound, octave block by octave block
+    // FP64 scan: a geometric window around the slope estimate (moved until it holds
+    // the crossing), then linear refinement until the exact pass accepts the bracket
     if (stats) stats->fallbacks++;
-    double scale = 1.0;
     for (int rep = 0; rep < 64; ++rep) {
-      k_gap_set<<<1, 1, 0, s>>>(gsc.ctx, kGapActive, kPlanGeo, scale);
+      k_gap_set<<<1, 1, 0, s>>>(gsc.ctx, kGapActive, kPlanGeo, rep == 0 ? 1 : 0);
       k_gap_scan64<T><<<G, kThreads, 0, s>>>(a, kPlanGeo, 0);
       nl += 2;
       PDLP_LAUNCH_CHECK();
       PDLP_CUDA_CHECK(cudaMemcpyAsync(&h, gsc.ctx, sizeof(GapCtx), cudaMemcpyDeviceToHost, s));
       PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
       if (h.state != kGapNeedMore) break;
-      scale = ldexp(scale, kGapQ);
     }
     for (int rep = 0; rep < 80 && h.state == kGapActive; ++rep) {
       k_gap_clear_cand<<<1, 1, 0, s>>>(gsc.ctx);
@@ -912,10 +919,11 @@ double normalized_gap(const PointRef<T>& z, const T* x_ref, const T* y_ref, doub
         PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
         break;
       }
-      k_gap_set<<<1, 1, 0, s>>>(gsc.ctx, kGapActive, kPlanLin, 1.0);
+      k_gap_set<<<1, 1, 0, s>>>(gsc.ctx, kGapActive, kPlanLin, 0);
       k_gap_scan64<T><<<G, kThreads, 0, s>>>(a, kPlanLin, 1);
       nl += 2;
       PDLP_LAUNCH_CHECK();
+      h.state = kGapActive;  // the next pass re-reads the device state
     }
     if (h.state != kGapDone) {
       char buf[320];

@@ -242,3 +242,15 @@ def test_full_size_powerlaw_first_iterations(pkg):
     errs = GH.trace_errors(res.trace, ora.trace)
     assert all(e["restart_same"] for e in errs)
     assert max(e["ez"] for e in errs) <= TRACE_TOL, errs
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_every_gap_evaluation_resolves(pkg, precision):
+    """Over 1500 iterations of the power-law shape (10% free columns, 40% equality
+    rows), every normalized-gap evaluation of the restart scheme is resolved by the
+    bracket search (no NaN fallback), in both precisions."""
+    inst = lpgen.config1(scale=0.05)
+    res = pkg.solve_instance(inst, max_iters=1500, eps_rel_kkt=0.0, precision=precision)
+    st = res.stats
+    assert st["gap_evals"] > 20
+    assert st["gap_failures"] == 0, st.get("gap_failure_message")
