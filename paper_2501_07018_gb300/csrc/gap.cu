@@ -424,7 +424,9 @@ __global__ void __launch_bounds__(kThreads) k_gap_pass0(GapArgs<T> a, double ome
     c->mu = 0.0;
     c->state = kGapDone;
   } else {
-    c->s_lb = c->r / sqrt(c->slope2);
+    // r / slope is a lower bound of the crossing; the slope is summed in FP32, so
+    // back off by a margin far above its rounding error
+    c->s_lb = (1.0 - 1e-4) * c->r / sqrt(c->slope2);
     c->s_base = c->s_lb;
     c->state = kGapActive;
   }
@@ -442,13 +444,14 @@ __device__ void gap_update_bracket(GapCtx* c, const double* d2, const double* s_
     }
   if (plan == kPlanGeo) {
     // points s_base * 2^(q - kGapQ/2); a crossing off either end moves the window
+    // (the window spans 2^(kGapQ-1); moving it by that much makes windows abut)
     if (first < 0) {
-      c->s_base = ldexp(c->s_base, kGapQ);
+      c->s_base = ldexp(c->s_base, kGapQ - 1);
       c->state = kGapNeedMore;
       return;
     }
     if (first == 0) {
-      c->s_base = ldexp(c->s_base, -kGapQ);
+      c->s_base = ldexp(c->s_base, -(kGapQ - 1));
       c->state = kGapNeedMore;
       return;
     }
