@@ -168,6 +168,31 @@ int pdlp_kkt(int64_t m, int64_t n, const pdlp_csr* A, const double* c, const dou
              const double* uc, const double* lv, const double* uv, const double* x,
              const double* y, const pdlp_params* p, double* out);
 
+/* The measures of pdlp_kkt for a point whose products A x and A'y the caller already
+ * holds, computed WITHOUT ALLOCATING ANY MEMORY.  The paper has no counterpart: this
+ * entry point exists for callers that cannot let a library allocate device memory
+ * mid-run -- for instance an application whose memory manager owns the whole device
+ * (a framework pool or a preallocated arena) or a loop with a fixed latency budget
+ * where a cudaMalloc/cudaFree could block -- but still want the optimality
+ * measures of an iterate they computed themselves.
+ *   All arrays are DEVICE arrays of the current device: c, lv, uv, x, aty [n];
+ *   lc, uc, y, ax [m] (ax = A x, aty = A'y of the LP as given).  out[11] is host
+ *   memory and receives the values in pdlp_kkt's order.  cuda_stream may be NULL.
+ *   m in [0, 2^31-1], n in [1, 2^31-1]; other sizes return PDLP_INVALID_ARGUMENT.
+ * Scratch: the per-CTA partial sums (at most 1024 CTAs), the arrival counter and the
+ * result live in one fixed file-scope device array of about 74 KB, which every GPU
+ * that loads the library keeps until the process exits; its size does not depend on
+ * m or n.  The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress) and caches it; make that first call before any stream
+ * capture.  Every call clears the counter and overwrites the rest.  All calls share
+ * the one array: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race and give wrong results, so serialize them.  The call blocks until
+ * its result is in out.  Returns 0, PDLP_INVALID_ARGUMENT or PDLP_CUDA_ERROR. */
+int pdlp_kkt_products_noalloc(int64_t m, int64_t n, const double* c, const double* lc,
+                              const double* uc, const double* lv, const double* uv,
+                              const double* x, const double* y, const double* ax,
+                              const double* aty, void* cuda_stream, double* out);
+
 /* Message for the last nonzero return of a call made by this thread. */
 const char* pdlp_last_error(void);
 

@@ -107,6 +107,8 @@ def load_library(path: str | None = None):
     lib.pdlp_kkt.argtypes = [i64, i64, ctypes.POINTER(Csr), P, P, P, P, P, P, P,
                              ctypes.POINTER(Params), P]
     lib.pdlp_kkt.restype = ctypes.c_int
+    lib.pdlp_kkt_products_noalloc.argtypes = [i64, i64, P, P, P, P, P, P, P, P, P, P, P]
+    lib.pdlp_kkt_products_noalloc.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -305,4 +307,22 @@ def kkt(m, n, row_ptr, col_idx, val, c, lc, uc, lv, uv, x, y, **params) -> dict:
     prm = _params_for(on_device, params)
     out = np.zeros(len(KKT_FIELDS))
     _check(lib.pdlp_kkt(m, n, ctypes.byref(A), *vecs, *pts, ctypes.byref(prm), out.ctypes.data))
+    return dict(zip(KKT_FIELDS, out.tolist()))
+
+
+def kkt_products_noalloc(m, n, c, lc, uc, lv, uv, x, y, ax, aty, cuda_stream=None) -> dict:
+    """pdlp_kkt_products_noalloc: the measures of ``kkt`` for a point whose products
+    ax = A x and aty = A'y are given, without any allocation by the library.  Every
+    array must be a float64 CUDA tensor on the current device."""
+    import torch
+
+    lib = load_library()
+    args = [c, lc, uc, lv, uv, x, y, ax, aty]
+    for t in args:
+        if not (_is_cuda_tensor(t) and t.dtype == torch.float64 and t.is_contiguous()):
+            raise TypeError("every array must be a contiguous float64 CUDA tensor")
+    stream = cuda_stream if cuda_stream is not None else torch.cuda.current_stream().cuda_stream
+    out = np.zeros(len(KKT_FIELDS))
+    _check(lib.pdlp_kkt_products_noalloc(m, n, *[t.data_ptr() if t.numel() else None for t in args],
+                                         stream, out.ctypes.data))
     return dict(zip(KKT_FIELDS, out.tolist()))

@@ -20,6 +20,7 @@ struct PdlpError : public std::runtime_error {
 };
 
 void set_last_error(const std::string& msg);
+void set_last_error_cstr(const char* msg, const char* detail);  // never allocates
 
 #define PDLP_CUDA_CHECK(expr)                                                          \
   do {                                                                                 \

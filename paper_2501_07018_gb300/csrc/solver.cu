@@ -21,8 +21,18 @@
 
 namespace pdlp {
 
-static thread_local std::string g_last_error;
-void set_last_error(const std::string& msg) { g_last_error = msg; }
+// message of the last failed call of this thread, in a fixed buffer so that recording
+// an error never allocates
+static thread_local char g_last_error[1024] = {0};
+void set_last_error(const std::string& msg) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg.c_str());
+}
+void set_last_error_cstr(const char* msg, const char* detail) {
+  if (detail)
+    std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s", msg, detail);
+  else
+    std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
+}
 
 __device__ __forceinline__ int64_t sgi() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ int64_t sgs() { return (int64_t)gridDim.x * blockDim.x; }
@@ -967,7 +977,7 @@ void pdlp_params_default(pdlp_params* p) {
   p->verbose = 0;
 }
 
-const char* pdlp_last_error(void) { return g_last_error.c_str(); }
+const char* pdlp_last_error(void) { return g_last_error; }
 
 int pdlp_solve(int64_t m, int64_t n, const pdlp_csr* A, const double* c, const double* lc,
                const double* uc, const double* lv, const double* uv, const pdlp_params* p,
