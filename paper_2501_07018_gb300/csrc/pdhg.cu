@@ -169,7 +169,12 @@ __device__ __forceinline__ void row_epilogue(const EpiCtx<T>& e, const EpiIn<T>&
     const T axo = in.a, yo = in.b;
     const T q = (T)2 * v - axo;
     const T yh = yo - e.sigma * q;
-    const T yn = yh - clampv<T>(yh, -e.sigma * in.d, -e.sigma * in.c);
+    // Sec. 2's case analysis of Eq. (3b): y' = yh + sigma uc if that is negative,
+    // yh + sigma lc if that is positive, else 0 (a free row gives +-inf and lands on
+    // 0); one rounding each and exact in sign
+    const T tu = fma(e.sigma, in.d, yh);
+    const T tl = fma(e.sigma, in.c, yh);
+    const T yn = tu < (T)0 ? tu : (tl > (T)0 ? tl : (T)0);
     e.out0[row] = v;
     e.out1[row] = yn;
     const A dy = (A)yn - (A)yo;
