@@ -48,6 +48,19 @@ used):
       -A(2x'-x), the signed term (y'-y)'A(x'-x) is negative on typical steps, and the
       literal formula then never limits eta (eta grows without bound and the
       iteration diverges).  With the magnitude, eta_bar >= 1/||A||_2 still holds.
+  R20 The dual feasibility problem of Sec. 5 is solved as the LP with every finite
+      bound set to 0: its dual objective vanishes on the dual feasible set, which is
+      unchanged because Y and R depend only on which bounds are finite.
+  R21 Feasibility polishing (Algorithm 4): the pause test uses the relative gap of
+      Eq. (8) of the average iterate since the last restart, after the k-th
+      iteration's own checks and restart (right after a restart that average is the
+      restart point); each polishing phase is a fresh PDLP run (own iteration count
+      for the step-size factors, checks and restarts; z^{n,0} = its start) with
+      normal PDLP's current primal weight and step estimate; "primal (dual)
+      constraint violation below the termination tolerance" is the primal (dual) half
+      of the termination criteria in force, tested on the restart candidate at the
+      checks and at the phase's last iteration; the primal phase's output is its
+      returned candidate, the dual phase's likewise even when it hits its budget.
 """
 from __future__ import annotations
 
@@ -90,6 +103,7 @@ class Params:
     fixed_step: float | None = None  # constant eta, no adaptive step (Chambolle-Pock)
     fixed_omega: float | None = None
     restarts: bool = True
+    feasibility_polishing: bool = False  # Algorithm 4 (Sec. 5)
 
 
 # ----------------------------------------------------------------------------
@@ -470,9 +484,147 @@ class Result:
     trace: list
 
 
+class PdlpRun:
+    """One run of Algorithm 1 (Algorithm 2 steps, the restart scheme of Sec. 3,
+    Algorithm 3's primal weight) on the scaled LP ``lp``, from the start (x, y) with
+    primal weight ``omega`` and step estimate ``eta_hat``.
+
+    ``goal(x, y)`` is the termination test of a candidate (scaled point, R9);
+    ``max_iters`` caps the accepted iterations.  ``run(pause_at)`` advances until the
+    goal is met, the cap is reached or a step fails -- returning (status, x, y) -- or,
+    if ``pause_at`` is given, until ``pause_at`` iterations are complete (with that
+    iteration's checks and restart done), returning None; the state stays in the
+    object, so a paused run continues where it stopped."""
+
+    def __init__(self, lp, prm: Params, x, y, omega, eta_hat, goal, max_iters, trace_iters=0):
+        m, n = lp.A.shape
+        self.lp, self.prm, self.goal, self.max_iters = lp, prm, goal, max_iters
+        self.m, self.n = m, n
+        self.x, self.y = np.array(x, dtype=float), np.array(y, dtype=float)
+        self.Ax, self.ATy = lp.A @ self.x, lp.AT @ self.y
+        self.omega, self.eta_hat = omega, eta_hat
+        self.k = self.t = 0
+        self.x0, self.y0 = self.x.copy(), self.y.copy()  # z^{n,0}
+        self.mu_ref = None  # mu(z^{n,0}, z^{n-1,0})  (R5, R7)
+        self.mu_c_prev = math.inf  # R6
+        self._zero_sums()
+        self.stats = dict(iterations=0, attempts=0, rejected_steps=0, restarts=[0, 0, 0],
+                          kkt_passes=0.0)
+        self.trace = []
+        self.trace_iters = trace_iters
+        self.started = False
+
+    def _zero_sums(self):
+        self.Sx, self.Sy = np.zeros(self.n), np.zeros(self.m)
+        self.SAx, self.SATy = np.zeros(self.m), np.zeros(self.n)
+        self.W = 0.0
+
+    def average(self):
+        """Running weighted average since the last restart (Algorithm 1); right after
+        a restart (no step since) it is the restart point itself."""
+        if self.W == 0.0:
+            return self.x.copy(), self.y.copy()
+        return self.Sx / self.W, self.Sy / self.W
+
+    def run(self, pause_at=None):
+        prm, lp = self.prm, self.lp
+        if not self.started:
+            self.started = True
+            # termination check before the first step (Sec. 3, "Periodic checks")
+            if self.goal(self.x, self.y):
+                return OPTIMAL, self.x, self.y
+        while True:
+            if pause_at is not None and self.k >= pause_at:
+                return None
+            x, y, Ax, ATy, omega = self.x, self.y, self.Ax, self.ATy, self.omega
+            if prm.fixed_step is not None:
+                tau, sig = prm.fixed_step / omega, prm.fixed_step * omega
+                xn = primal_step(x, ATy, lp.c, lp.lv, lp.uv, tau)
+                Axn = lp.A @ xn
+                yn = dual_step(y, Ax, Axn, lp.lc, lp.uc, sig)
+                eta, eta_new, attempts, ok = prm.fixed_step, prm.fixed_step, 1, True
+            else:
+                xn, yn, Axn, eta, eta_new, attempts, ok = adaptive_step(
+                    lp, x, y, Ax, ATy, omega, self.eta_hat, self.k, prm.max_step_retries)
+            self.stats["attempts"] += attempts
+            self.stats["rejected_steps"] += attempts - 1
+            self.stats["kkt_passes"] += 0.5 * attempts + 0.5
+            if not ok:
+                return NUMERICAL_ERROR, x, y
+            ATyn = lp.AT @ yn
+            # running weighted average since the last restart (Algorithm 1)
+            self.Sx += eta * xn
+            self.Sy += eta * yn
+            self.SAx += eta * Axn
+            self.SATy += eta * ATyn
+            self.W += eta
+            self.x, self.y, self.Ax, self.ATy = xn, yn, Axn, ATyn
+            self.eta_hat = eta_new
+            self.t += 1
+            self.k += 1
+            k, t = self.k, self.t
+            self.stats["iterations"] = k
+            rec = None
+            if len(self.trace) < self.trace_iters:
+                rec = dict(k=k, x=xn.copy(), y=yn.copy(), eta=eta, omega=omega,
+                           eta_hat=eta_new, attempts=attempts, restart=RESTART_NONE,
+                           mu_cur=math.nan, mu_avg=math.nan)
+                self.trace.append(rec)
+
+            is_check = (k % prm.check_period) == 0  # R4
+            is_art = prm.restarts and (t >= prm.beta_art * k)
+            is_limit = k >= self.max_iters
+            if not (is_check or is_art or is_limit):
+                continue
+            # GetRestartCandidate (Sec. 3): current iterate vs the average (R8, R18)
+            W = self.W
+            xa, ya, Axa, ATya = self.Sx / W, self.Sy / W, self.SAx / W, self.SATy / W
+            x0, y0 = self.x0, self.y0
+            mu_cur = normalized_gap(lp, xn, yn, Axn, ATyn, x0, y0, omega)
+            mu_avg = normalized_gap(lp, xa, ya, Axa, ATya, x0, y0, omega)
+            if mu_cur < mu_avg:
+                cand, mu_c = (xn, yn, Axn, ATyn), mu_cur
+            else:
+                cand, mu_c = (xa, ya, Axa, ATya), mu_avg
+            if rec is not None:
+                rec["mu_cur"], rec["mu_avg"] = mu_cur, mu_avg
+            if is_check or is_limit:  # R9
+                if self.goal(cand[0], cand[1]):
+                    return OPTIMAL, cand[0], cand[1]
+                if is_limit:
+                    return ITERATION_LIMIT, cand[0], cand[1]
+            kind = RESTART_NONE
+            if prm.restarts and is_check and self.mu_ref is not None:
+                if mu_c <= prm.beta_suff * self.mu_ref:
+                    kind = RESTART_SUFFICIENT
+                elif mu_c <= prm.beta_nec * self.mu_ref and mu_c > self.mu_c_prev:
+                    kind = RESTART_NECESSARY
+            if kind == RESTART_NONE and is_art:
+                kind = RESTART_ARTIFICIAL
+            if is_check:
+                self.mu_c_prev = mu_c
+            if kind == RESTART_NONE:
+                continue
+            # restart the outer loop: z^{n+1,0} <- candidate, eta_hat carried
+            self.stats["restarts"][kind - 1] += 1
+            if rec is not None:
+                rec["restart"] = kind
+            self.x, self.y, self.Ax, self.ATy = (v.copy() for v in cand)
+            if prm.fixed_omega is None:
+                self.omega = primal_weight_update(self.x, self.y, x0, y0, omega, prm.theta,
+                                                  prm.eps_zero)
+            self.mu_ref = normalized_gap(lp, self.x, self.y, self.Ax, self.ATy, x0, y0,
+                                         self.omega)  # R7
+            self.x0, self.y0 = self.x.copy(), self.y.copy()
+            self.t = 0
+            self.mu_c_prev = math.inf
+            self._zero_sums()
+
+
 def solve(inst, prm: Params | None = None, trace_iters: int = 0, lp: ScaledLP | None = None,
           x_init=None, y_init=None) -> Result:
-    """Algorithm 1 after preconditioning.  ``trace_iters`` > 0 records, for each of the
+    """Algorithm 1 after preconditioning (with feasibility polishing, Algorithm 4,
+    when ``prm.feasibility_polishing``).  ``trace_iters`` > 0 records, for each of the
     first accepted iterations, the scaled iterate and the step/weight scalars.
     ``x_init``/``y_init`` (scaled space) override R1's starting point."""
     prm = prm or Params()
@@ -489,110 +641,101 @@ def solve(inst, prm: Params | None = None, trace_iters: int = 0, lp: ScaledLP | 
     # R1
     x = proj_box(np.zeros(n), lp.lv, lp.uv) if x_init is None else np.array(x_init, dtype=float)
     y = np.zeros(m) if y_init is None else np.array(y_init, dtype=float)
-    Ax = lp.A @ x
-    ATy = lp.AT @ y
-    k = t = 0
-    n_outer = 0
-    x0, y0 = x.copy(), y.copy()  # z^{n,0}
-    mu_ref = None  # mu(z^{n,0}, z^{n-1,0})  (R5, R7)
-    mu_c_prev = math.inf  # R6
-    Sx, Sy, SAx, SATy, W = np.zeros(n), np.zeros(m), np.zeros(m), np.zeros(n), 0.0
-    stats = dict(iterations=0, attempts=0, rejected_steps=0, restarts=[0, 0, 0],
-                 kkt_passes=0.0)
-    trace = []
 
-    def unscale(xs, ys):
-        return lp.d2 * xs, lp.d1 * ys
+    def measures(xs, ys):
+        return kkt_stats(inst, lp.A_orig, lp.d2 * xs, lp.d1 * ys)
 
-    def finish(status, xs, ys):
-        xu, yu = unscale(xs, ys)
-        st = kkt_stats(inst, lp.A_orig, xu, yu)
-        stats.update(st)
-        stats.update(iterations=k, omega=omega, eta_hat=eta_hat)
-        return Result(status, xu, yu, stats, trace)
+    run = PdlpRun(lp, prm, x, y, omega, eta_hat, lambda xs, ys: converged(measures(xs, ys), prm),
+                  prm.max_iters, trace_iters)
+    polish = None
+    if prm.feasibility_polishing:
+        status, xs, ys, polish = _solve_polished(lp, prm, run, measures)
+    else:
+        status, xs, ys = run.run()
+    stats = dict(run.stats)
+    stats.update(measures(xs, ys))
+    stats.update(iterations=run.k, omega=run.omega, eta_hat=run.eta_hat)
+    if polish is not None:
+        stats["polish"] = polish
+        stats["polish_primal_iters"] = sum(p["primal_iters"] for p in polish)
+        stats["polish_dual_iters"] = sum(p["dual_iters"] for p in polish)
+    return Result(status, lp.d2 * xs, lp.d1 * ys, stats, run.trace)
 
-    # termination check before the first step (Sec. 3, "Periodic checks")
-    xu, yu = unscale(x, y)
-    if converged(kkt_stats(inst, lp.A_orig, xu, yu), prm):
-        return finish(OPTIMAL, x, y)
 
+# ----------------------------------------------------------------------------
+# feasibility polishing (Sec. 5, Algorithm 4)
+# ----------------------------------------------------------------------------
+
+def primal_feasibility_lp(lp: ScaledLP) -> ScaledLP:
+    """The primal feasibility problem of Sec. 5: the LP with objective 0."""
+    return dataclasses.replace(lp, c=np.zeros_like(lp.c))
+
+
+def dual_feasibility_lp(lp: ScaledLP) -> ScaledLP:
+    """The LP whose dual is the dual feasibility problem of Sec. 5: every finite bound
+    set to 0 (infinite ones kept), so that p(.) vanishes on the dual feasible set while
+    the sets Y and R, which depend only on which bounds are finite, are unchanged (R20)."""
+    z = lambda v: np.where(np.isfinite(v), 0.0, v)  # noqa: E731
+    return dataclasses.replace(lp, lc=z(lp.lc), uc=z(lp.uc), lv=z(lp.lv), uv=z(lp.uv))
+
+
+def primal_feasible(st, prm: Params):
+    """The primal half of the termination criteria."""
+    if prm.termination_mode == 0:
+        return st["rel_primal"] <= prm.eps_rel_kkt
+    return st["primal_res_inf"] <= prm.eps_abs_feas
+
+
+def dual_feasible(st, prm: Params):
+    """The dual half of the termination criteria."""
+    if prm.termination_mode == 0:
+        return st["rel_dual"] <= prm.eps_rel_kkt
+    return st["dual_res_inf"] <= prm.eps_abs_feas
+
+
+def polish_pauses():
+    """Iteration counts after which normal PDLP may pause: 100, 200, 400, ... (Alg. 4)."""
+    k = 100
     while True:
-        step_omega = omega
-        if prm.fixed_step is not None:
-            tau, sig = prm.fixed_step / omega, prm.fixed_step * omega
-            xn = primal_step(x, ATy, lp.c, lp.lv, lp.uv, tau)
-            Axn = lp.A @ xn
-            yn = dual_step(y, Ax, Axn, lp.lc, lp.uc, sig)
-            eta, eta_new, attempts, ok = prm.fixed_step, prm.fixed_step, 1, True
-        else:
-            xn, yn, Axn, eta, eta_new, attempts, ok = adaptive_step(
-                lp, x, y, Ax, ATy, omega, eta_hat, k, prm.max_step_retries)
-        stats["attempts"] += attempts
-        stats["rejected_steps"] += attempts - 1
-        stats["kkt_passes"] += 0.5 * attempts + 0.5
-        if not ok:
-            return finish(NUMERICAL_ERROR, x, y)
-        ATyn = lp.AT @ yn
-        # running weighted average since the last restart (Algorithm 1)
-        Sx += eta * xn
-        Sy += eta * yn
-        SAx += eta * Axn
-        SATy += eta * ATyn
-        W += eta
-        x, y, Ax, ATy = xn, yn, Axn, ATyn
-        eta_hat = eta_new
-        t += 1
-        k += 1
-        rec = None
-        if len(trace) < trace_iters:
-            rec = dict(k=k, x=x.copy(), y=y.copy(), eta=eta, omega=step_omega,
-                       eta_hat=eta_hat, attempts=attempts, restart=RESTART_NONE,
-                       mu_cur=math.nan, mu_avg=math.nan)
-            trace.append(rec)
+        yield k
+        k *= 2
 
-        is_check = (k % prm.check_period) == 0  # R4
-        is_art = prm.restarts and (t >= prm.beta_art * k)
-        is_limit = k >= prm.max_iters
-        if not (is_check or is_art or is_limit):
+
+def _solve_polished(lp, prm: Params, run: PdlpRun, measures):
+    """Algorithm 4.  Normal PDLP (``run``) pauses after k = 100, 200, 400, ... iterations
+    when the relative gap of Eq. (8) of its average iterate (x^k, y^k) is below
+    eps_rel_gap.  Then PDLP on the primal feasibility problem runs from (x^k, 0), and
+    PDLP on the dual feasibility problem from (0, y^k), each with normal PDLP's current
+    primal weight and step estimate, for at most k/8 iterations and with its own
+    iteration count (R21).  If the primal phase does not reach primal feasibility,
+    normal PDLP resumes; otherwise the pair (x~ from the primal phase, y~ from the
+    dual phase) is returned if it meets the termination criteria, else normal PDLP
+    resumes.  Returns (status, x, y, log) with one log entry per pause."""
+    m, n = run.m, run.n
+    lp_p, lp_d = primal_feasibility_lp(lp), dual_feasibility_lp(lp)
+    log = []
+    for k_pause in polish_pauses():
+        out = run.run(pause_at=k_pause)
+        if out is not None:
+            return (*out, log)
+        xk, yk = run.average()
+        gap = measures(xk, yk)["paper_gap"]
+        entry = dict(k=k_pause, paper_gap=gap, primal_iters=0, primal_ok=False, dual_iters=0,
+                     dual_ok=False, accepted=False)
+        log.append(entry)
+        if not gap < prm.eps_rel_gap:
             continue
-        # GetRestartCandidate (Sec. 3): current iterate vs the average (R8, R18)
-        xa, ya, Axa, ATya = Sx / W, Sy / W, SAx / W, SATy / W
-        mu_cur = normalized_gap(lp, x, y, Ax, ATy, x0, y0, omega)
-        mu_avg = normalized_gap(lp, xa, ya, Axa, ATya, x0, y0, omega)
-        if mu_cur < mu_avg:
-            cand, mu_c = (x, y, Ax, ATy), mu_cur
-        else:
-            cand, mu_c = (xa, ya, Axa, ATya), mu_avg
-        if rec is not None:
-            rec["mu_cur"], rec["mu_avg"] = mu_cur, mu_avg
-        if is_check or is_limit:  # R9
-            xu, yu = unscale(cand[0], cand[1])
-            if converged(kkt_stats(inst, lp.A_orig, xu, yu), prm):
-                return finish(OPTIMAL, cand[0], cand[1])
-            if is_limit:
-                return finish(ITERATION_LIMIT, cand[0], cand[1])
-        kind = RESTART_NONE
-        if prm.restarts and is_check and mu_ref is not None:
-            if mu_c <= prm.beta_suff * mu_ref:
-                kind = RESTART_SUFFICIENT
-            elif mu_c <= prm.beta_nec * mu_ref and mu_c > mu_c_prev:
-                kind = RESTART_NECESSARY
-        if kind == RESTART_NONE and is_art:
-            kind = RESTART_ARTIFICIAL
-        if is_check:
-            mu_c_prev = mu_c
-        if kind == RESTART_NONE:
+        budget = k_pause // 8
+        pr = PdlpRun(lp_p, prm, xk, np.zeros(m), run.omega, run.eta_hat,
+                     lambda xs, ys: primal_feasible(measures(xs, ys), prm), budget)
+        st_p, x_t, _ = pr.run()
+        entry.update(primal_iters=pr.k, primal_ok=st_p == OPTIMAL)
+        if st_p != OPTIMAL:
             continue
-        # restart the outer loop: z^{n+1,0} <- candidate, eta_hat carried
-        stats["restarts"][kind - 1] += 1
-        if rec is not None:
-            rec["restart"] = kind
-        x, y, Ax, ATy = (v.copy() for v in cand)
-        if prm.fixed_omega is None:
-            omega = primal_weight_update(x, y, x0, y0, omega, prm.theta, prm.eps_zero)
-        mu_ref = normalized_gap(lp, x, y, Ax, ATy, x0, y0, omega)  # R7
-        x0, y0 = x.copy(), y.copy()
-        n_outer += 1
-        t = 0
-        mu_c_prev = math.inf
-        Sx, Sy, SAx, SATy, W = np.zeros(n), np.zeros(m), np.zeros(m), np.zeros(n), 0.0
+        dr = PdlpRun(lp_d, prm, np.zeros(n), yk, run.omega, run.eta_hat,
+                     lambda xs, ys: dual_feasible(measures(xs, ys), prm), budget)
+        st_d, _, y_t = dr.run()
+        entry.update(dual_iters=dr.k, dual_ok=st_d == OPTIMAL)
+        if converged(measures(x_t, y_t), prm):
+            entry["accepted"] = True
+            return OPTIMAL, x_t, y_t, log

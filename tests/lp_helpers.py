@@ -237,3 +237,34 @@ def sample_trust_region_max(lp, x, y, A_dense, r, omega, rng, nsamp=400000):
     L_x_yh = lp.c @ x - yh @ Ax - _p_rows(lp, yh)
     L_xh_y = xh @ lp.c - (xh @ A_dense.T) @ y - _p_rows(lp, y[None, :])[0]
     return float(np.max(L_x_yh - L_xh_y)) if xh.shape[0] else -math.inf
+
+
+def lp_with_feasible_pair(rng, m, n, density=0.4):
+    """A random LP with every kind of bound (two-sided, equality, one-sided, free rows;
+    boxed, one-sided, free columns) built around a primal feasible x_F and a dual
+    feasible y_F (sign pattern of Sec. 2's Y, reduced costs r_F in R, c = A'y_F + r_F),
+    so that it has an optimum.  Returns (inst, x_F, y_F)."""
+    A = rng.standard_normal((m, n)) * (rng.random((m, n)) < density)
+    for i in range(m):  # no empty row
+        if not A[i].any():
+            A[i, rng.integers(n)] = 1.0
+    x_F = rng.uniform(-2, 2, n)
+    ax = A @ x_F
+    kind_r = rng.integers(0, 5, m)  # 0 two-sided, 1 equality, 2 lower only, 3 upper only, 4 free
+    lc = np.where(np.isin(kind_r, (0, 2)), ax - rng.uniform(0, 1, m), -np.inf)
+    uc = np.where(np.isin(kind_r, (0, 3)), ax + rng.uniform(0, 1, m), np.inf)
+    lc = np.where(kind_r == 1, ax, lc)
+    uc = np.where(kind_r == 1, ax, uc)
+    y_F = rng.standard_normal(m)
+    y_F = np.where(kind_r == 2, np.abs(y_F), y_F)
+    y_F = np.where(kind_r == 3, -np.abs(y_F), y_F)
+    y_F = np.where(kind_r == 4, 0.0, y_F)
+    kind_c = rng.integers(0, 4, n)  # 0 boxed, 1 lower only, 2 upper only, 3 free
+    lv = np.where(np.isin(kind_c, (0, 1)), x_F - rng.uniform(0, 2, n), -np.inf)
+    uv = np.where(np.isin(kind_c, (0, 2)), x_F + rng.uniform(0, 2, n), np.inf)
+    r_F = rng.standard_normal(n)
+    r_F = np.where(kind_c == 1, np.abs(r_F), r_F)
+    r_F = np.where(kind_c == 2, -np.abs(r_F), r_F)
+    r_F = np.where(kind_c == 3, 0.0, r_F)
+    c = A.T @ y_F + r_F
+    return make_lp(A, c, lc, uc, lv, uv, name="feasible-pair"), x_F, y_F

@@ -70,3 +70,41 @@ def test_dual_objective_swapped_bounds_is_caught(monkeypatch):
     monkeypatch.setattr(O, "p_fn", bad)
     with pytest.raises(AssertionError):
         P.test_weak_duality_any_dual_point()
+
+
+# --- feasibility polishing (Sec. 5, Algorithm 4) -----------------------------------
+from tests import test_oracle_polishing as PP  # noqa: E402
+
+
+def test_primal_phase_keeping_the_objective_is_caught(monkeypatch):
+    monkeypatch.setattr(O, "primal_feasibility_lp", lambda lp: lp)
+    with pytest.raises(AssertionError):
+        PP.test_phases_never_move_away_from_their_saddle_points(3)
+
+
+def test_dual_phase_zeroing_infinite_bounds_is_caught(monkeypatch):
+    import dataclasses
+
+    def bad(lp):
+        z = np.zeros_like
+        return dataclasses.replace(lp, lc=z(lp.lc), uc=z(lp.uc), lv=z(lp.lv), uv=z(lp.uv))
+    monkeypatch.setattr(O, "dual_feasibility_lp", bad)
+    with pytest.raises(AssertionError):
+        PP.test_feasibility_problems_of_sec5()
+
+
+def test_dual_phase_keeping_the_bounds_is_caught(monkeypatch):
+    monkeypatch.setattr(O, "dual_feasibility_lp", lambda lp: lp)
+    with pytest.raises(AssertionError):
+        PP.test_phases_never_move_away_from_their_saddle_points(3)
+
+
+def test_wrong_pause_schedule_is_caught(monkeypatch):
+    def bad():
+        k = 100
+        while True:
+            yield k
+            k += 100
+    monkeypatch.setattr(O, "polish_pauses", bad)
+    with pytest.raises(AssertionError):
+        PP.test_pause_schedule_and_phase_budgets()
