@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--iters-per-step", type=int, default=5000)
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the LP (testing only)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
+                    help="arithmetic of the PDHG loop (fp32 = FP32 bulk, FP64 checks)")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--cpu-sample-child", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -76,9 +78,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_from_profiles(kernel_key, scale_units):
+def traffic_from_profiles(kernel_key, units):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel source; null otherwise."""
+    current kernel source, scaled from the captured launch's algorithmic bytes to
+    `units` algorithmic bytes; null otherwise."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -88,7 +91,7 @@ def traffic_from_profiles(kernel_key, scale_units):
     e = t.get(kernel_key)
     if not e or e.get("source_sha") != kernel_source_hash():
         return None
-    return e["dram_bytes_per_launch"] * scale_units / e.get("units", scale_units)
+    return e["dram_bytes_per_launch"] * units / e["algorithmic_bytes_per_launch"]
 
 
 # ---------------------------------------------------------------------------
@@ -226,6 +229,21 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def aggregate_over_ranks(dist, secs, iters, launches, device):
+    """Whole-job figures of independent replicas: the slowest rank's seconds and the
+    iterations and kernel launches of all ranks (one all_reduce each; works on any
+    process-group backend, `dist` None for a single process)."""
+    import torch
+
+    t = torch.tensor([secs, float(iters), float(launches)], device=device, dtype=torch.float64)
+    if dist is None:
+        return secs, float(iters), float(launches)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1]), float(t[2])
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -249,8 +267,11 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     iters = args.iters_per_step
 
+    prec = pkg.FP64 if args.precision == "fp64" else pkg.FP32_BULK
+
     def step(profile=1):
-        return pkg.solve(inst.m, inst.n, *d, max_iters=iters, eps_rel_kkt=0.0, profile=profile)
+        return pkg.solve(inst.m, inst.n, *d, max_iters=iters, eps_rel_kkt=0.0, profile=profile,
+                         precision=prec)
 
     def barrier():
         if dist is not None:
@@ -279,45 +300,42 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks = clk.stop()
     secs = e0.elapsed_time(e1) / 1e3
-    t = torch.tensor([secs, float(agg["iterations"]), float(agg["kernel_launches"])], device="cuda",
-                     dtype=torch.float64)
-    if dist is not None:
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        secs_max, total_iters, total_launches = float(tmax[0]), float(t[1]), float(t[2])
-    else:
-        secs_max, total_iters, total_launches = secs, float(t[1]), float(t[2])
+    secs_max, total_iters, total_launches = aggregate_over_ranks(
+        dist, secs, agg["iterations"], agg["kernel_launches"], "cuda")
     value = total_iters / secs_max
 
     # dominant fused SpMV kernel (CUDA events inside the library, on the launching stream)
     st = last.stats
+    ctype = "double" if args.precision == "fp64" else "float"
     cand = []
     if agg["launches_spmv_a"]:
         cand.append(("spmv_a", agg["ms_spmv_a"], agg["launches_spmv_a"], st["bytes_spmv_a"],
-                     "k_spmv<double,kEpiDual>: A x' + dual step (Eq. 3b) + step-size sums"))
+                     f"k_spmv<{ctype},kEpiDual>: A x' + dual step (Eq. 3b) + step-size sums"))
     if agg["launches_spmv_at"]:
         cand.append(("spmv_at", agg["ms_spmv_at"], agg["launches_spmv_at"], st["bytes_spmv_at"],
-                     "k_spmv<double,kEpiAverage>: A'y' + running averages"))
+                     f"k_spmv<{ctype},kEpiAverage>: A'y' + running averages"))
     key, ms, launches, bytes_per, desc = max(cand, key=lambda c: c[1])
     per_launch_s = ms / launches / 1e3
     achieved = bytes_per / per_launch_s / 1e9
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else PEAK_FALLBACK_GBS
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic_from_profiles(key, 1.0),
+                "frac": achieved / peak,
+                "traffic": traffic_from_profiles(f"{key}_{args.precision}", bytes_per),
                 "kernel": desc, "algorithmic_bytes_per_launch": bytes_per,
                 "ms_per_launch": per_launch_s * 1e3,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"}
-    other = {c[0]: {"ms_per_launch": c[1] / c[2], "gbs": c[3] / (c[1] / c[2] / 1e3) / 1e9}
-             for c in cand}
+    other = {c[0]: {"ms_per_launch": c[1] / c[2], "gbs": c[3] / (c[1] / c[2] / 1e3) / 1e9,
+                    "algorithmic_bytes_per_launch": c[3], "launches": c[2],
+                    "share_of_step": c[1] / (1e3 * secs)} for c in cand}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * secs_max / args.steps,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if args.precision == "fp64" else "f32",
            "data": "synthetic",
            "config": {"workload": workload_name(inst), "iters_per_step": iters,
-                      "precision": "fp64", "inputs": "HBM-resident (torch CUDA tensors)",
+                      "precision": args.precision, "inputs": "HBM-resident (torch CUDA tensors)",
                       "l2": "no flush: the matrix (A and A' ~1.2 GB FP64) is far larger than L2",
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
            "roofline": roofline, "kernels": other, "clocks": clocks,
@@ -331,11 +349,11 @@ def run_ours(args):
     h2d = sum(a.nbytes for a in pinned)
     d2h = 8 * (inst.n + inst.m)
     e2e_steps = max(2, min(3, args.steps))
-    pkg.solve(inst.m, inst.n, *pinned, max_iters=iters, eps_rel_kkt=0.0)
+    pkg.solve(inst.m, inst.n, *pinned, max_iters=iters, eps_rel_kkt=0.0, precision=prec)
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        r = pkg.solve(inst.m, inst.n, *pinned, max_iters=iters, eps_rel_kkt=0.0)
+        r = pkg.solve(inst.m, inst.n, *pinned, max_iters=iters, eps_rel_kkt=0.0, precision=prec)
     t_e2e = time.perf_counter() - t0
     tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
     if dist is not None:
