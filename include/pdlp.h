@@ -90,7 +90,28 @@ typedef struct {
   double* trace_out;       /* host array [trace_iters * (PDLP_TRACE_HEADER + n + m)] */
   int profile;             /* 1: time the hot kernels with CUDA events (stats)       */
   int verbose;             /* 1: one line per check to stderr                        */
+  int feasibility_polishing; /* 1: Algorithm 4 (Sec. 5).  Normal PDLP pauses after
+                              k = 100, 200, 400, ... iterations when the relative gap
+                              (Eq. (8)) of its average iterate is < eps_rel_gap; PDLP
+                              then runs on the primal feasibility problem (objective
+                              0) from (x^k, 0) and, if that reaches the primal half
+                              of the termination criteria, on the dual feasibility
+                              problem (finite bounds set to 0) from (0, y^k), each
+                              for at most k/8 iterations with normal PDLP's current
+                              primal weight and step; the pair is returned when it
+                              meets the termination criteria, else normal PDLP
+                              resumes.  Default 0.                                  */
+  int64_t polish_log_cap;  /* rows available in polish_log                          */
+  double* polish_log;      /* host [polish_log_cap * PDLP_POLISH_LOG_COLS] or NULL:
+                              one row per pause (see PDLP_POLISH_LOG_COLS)          */
 } pdlp_params;
+
+/* Row of params->polish_log for one pause of Algorithm 4:
+ *   [0] k (normal iterations done), [1] relative gap (Eq. (8)) of the average
+ *   iterate, [2] primal-phase iterations, [3] 1 if the primal phase reached primal
+ *   feasibility, [4] dual-phase iterations, [5] 1 if the dual phase reached dual
+ *   feasibility, [6] 1 if the pair was returned.                                   */
+#define PDLP_POLISH_LOG_COLS 7
 
 /* Trace record of one accepted iteration k (scaled space, i.e. of the
  * preconditioned LP): PDLP_TRACE_HEADER doubles, then x[n], then y[m].
@@ -122,6 +143,9 @@ typedef struct {
   int64_t gap_failures;    /* ... left unresolved (mu treated as NaN: no restart by
                               criteria (i)/(ii) at that check; pdlp_last_error()
                               describes the last one)                              */
+  int64_t polish_pauses;   /* Algorithm 4: pauses of normal PDLP                     */
+  int64_t polish_primal_iters, polish_dual_iters; /* iterations of all phases      */
+  int64_t polish_accepted_k; /* k of the pause whose pair was returned, else 0     */
 } pdlp_stats;
 
 /* Fills *p with the defaults listed above. */

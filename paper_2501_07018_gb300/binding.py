@@ -21,6 +21,8 @@ STATUS_NAMES = {0: "OPTIMAL", 1: "ITERATION_LIMIT", 2: "TIME_LIMIT", 3: "PRIMAL_
                 4: "DUAL_INFEASIBLE", 5: "NUMERICAL_ERROR", -1: "INVALID_ARGUMENT",
                 -2: "OUT_OF_MEMORY", -3: "CUDA_ERROR"}
 FP64, FP32_BULK = 0, 1
+POLISH_LOG_COLS = 7   # PDLP_POLISH_LOG_COLS
+POLISH_LOG_CAP = 64   # pauses recorded per solve (k = 100 * 2^63 is never reached)
 
 
 class Csr(ctypes.Structure):
@@ -41,6 +43,8 @@ class Params(ctypes.Structure):
         ("inputs_on_device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
         ("trace_iters", ctypes.c_int64), ("trace_out", ctypes.c_void_p),
         ("profile", ctypes.c_int), ("verbose", ctypes.c_int),
+        ("feasibility_polishing", ctypes.c_int), ("polish_log_cap", ctypes.c_int64),
+        ("polish_log", ctypes.c_void_p),
     ]
 
 
@@ -64,6 +68,8 @@ class Stats(ctypes.Structure):
         ("bytes_spmv_a", ctypes.c_double), ("bytes_spmv_at", ctypes.c_double),
         ("gap_evals", ctypes.c_int64), ("gap_fallbacks", ctypes.c_int64),
         ("gap_failures", ctypes.c_int64),
+        ("polish_pauses", ctypes.c_int64), ("polish_primal_iters", ctypes.c_int64),
+        ("polish_dual_iters", ctypes.c_int64), ("polish_accepted_k", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -231,12 +237,22 @@ def solve(m, n, row_ptr, col_idx, val, c, lc, uc, lv, uv, trace_iters: int = 0,
         trace_buf = np.full((trace_iters, TRACE_HEADER + n + m), np.nan)
         prm.trace_iters = trace_iters
         prm.trace_out = trace_buf.ctypes.data
+    log_buf = None
+    if prm.feasibility_polishing:
+        log_buf = np.zeros((POLISH_LOG_CAP, POLISH_LOG_COLS))
+        prm.polish_log_cap = POLISH_LOG_CAP
+        prm.polish_log = log_buf.ctypes.data
     x, xp = mh.out(n)
     y, yp = mh.out(m)
     st = Stats()
     code = lib.pdlp_solve(m, n, ctypes.byref(A), *vecs, ctypes.byref(prm), xp, yp, ctypes.byref(st))
     _check(code)
     stats = st.as_dict()
+    if log_buf is not None:
+        rows = log_buf[:min(stats["polish_pauses"], POLISH_LOG_CAP)]
+        stats["polish"] = [dict(k=int(r[0]), paper_gap=r[1], primal_iters=int(r[2]),
+                                primal_ok=bool(r[3]), dual_iters=int(r[4]), dual_ok=bool(r[5]),
+                                accepted=bool(r[6])) for r in rows]
     if stats["gap_failures"]:
         stats["gap_failure_message"] = lib.pdlp_last_error().decode()
     trace = []

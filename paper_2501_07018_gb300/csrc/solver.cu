@@ -12,7 +12,9 @@
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <memory>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/pdlp.h"
@@ -488,19 +490,71 @@ struct EventTimer {
   }
 };
 
+// Termination test of a run: Algorithm 1 uses the full criteria; the phases of
+// Algorithm 4 use the primal or the dual half of them.
+enum Goal { kGoalOptimal = 0, kGoalPrimalFeasible = 1, kGoalDualFeasible = 2 };
+
+static bool goal_met(const KktResult& r, const pdlp_params& p, int goal) {
+  if (goal == kGoalPrimalFeasible)
+    return p.termination_mode == 0 ? r.rel_primal <= p.eps_rel_kkt : r.pres_inf <= p.eps_abs_feas;
+  if (goal == kGoalDualFeasible)
+    return p.termination_mode == 0 ? r.rel_dual <= p.eps_rel_kkt : r.dres_inf <= p.eps_abs_feas;
+  return converged(r, p);
+}
+
+enum RunOutcome { kRunDone, kRunLimit, kRunError, kRunTime, kRunPaused };
+
+// One PDLP run (Algorithm 1) on the device: its iterate slots and running sums, the
+// LP vectors it solves, z^{n,0}, the device-side scalars and the host-side restart
+// bookkeeping.  A paused run keeps all of it and continues where it stopped.
+template <class T>
+struct Run {
+  IterBuffers<T> b{};
+  T *X0 = nullptr, *Y0 = nullptr;
+  DevState* dst = nullptr;
+  DevState hs{};
+  int goal = kGoalOptimal;
+  int64_t max_iters = 0;
+  bool trace = false;
+  bool started = false, have_mu_ref = false;
+  double mu_ref = 0.0, mu_c_prev = INFINITY;
+  int64_t k = 0, t = 0, attempts_at_last = 0;
+  int64_t restarts[3] = {0, 0, 0};
+};
+
+template <class T>
+__global__ void k_start_point(const T* xs, const T* ys, T* x, T* y, T* x0, T* y0, int64_t m,
+                              int64_t n) {
+  for (int64_t j = sgi(); j < n; j += sgs()) {
+    const T v = xs ? xs[j] : (T)0;
+    x[j] = v;
+    x0[j] = v;
+  }
+  for (int64_t i = sgi(); i < m; i += sgs()) {
+    const T v = ys ? ys[i] : (T)0;
+    y[i] = v;
+    y0[i] = v;
+  }
+}
+
+// finite entries -> 0, infinite ones kept (the bounds of the dual feasibility problem)
+template <class T>
+__global__ void k_zero_finite(const T* in, T* out, int64_t len) {
+  for (int64_t i = sgi(); i < len; i += sgs()) out[i] = isfinite(in[i]) ? (T)0 : in[i];
+}
+
 template <class T>
 struct Solver {
   const pdlp_params& prm;
   cudaStream_t s;
   DeviceArena arena;
   Problem<T> P;
-  IterBuffers<T> b{};
-  T *X0 = nullptr, *Y0 = nullptr, *Xa = nullptr, *Ya = nullptr, *AXa = nullptr, *ATYa = nullptr;
-  DevState* dst = nullptr;
-  DevState hs{};
+  Run<T> main_run, pol_run;
+  // scratch shared by the runs (they advance one at a time on one stream)
+  T *Xa = nullptr, *Ya = nullptr, *AXa = nullptr, *ATYa = nullptr;
   double *part_primal = nullptr, *part_dual = nullptr;
   unsigned int* counters = nullptr;  // [0] spmv-A, [1] kkt, [2] gap, [3] dist2
-  int g_primal = 1, g_a = 1, g_at = 1, g_plain_a = 1, g_red = 1;
+  int g_primal = 1, g_a = 1, g_at = 1, g_plain_a = 1, g_plain_at = 1, g_red = 1;
   KktScratch kks{};
   GapScratch gsc{};
   double* dist_part = nullptr;
@@ -509,39 +563,26 @@ struct Solver {
   GapStats gap_stats;
   int64_t launches = 0;
   double ms_checks = 0.0;
+  Clock::time_point t_solve0;
+  // feasibility polishing (Algorithm 4)
+  T* c_zero = nullptr;                                     // objective of the primal problem
+  T *zlc = nullptr, *zuc = nullptr, *zlv = nullptr, *zuv = nullptr;  // bounds of the dual one
+  T *Xk = nullptr, *Yk = nullptr;                          // (x^k, y^k) of the pause
+  T *Xt = nullptr, *AXt = nullptr, *Yt = nullptr, *ATYt = nullptr;  // polished pair
 
   Solver(const pdlp_params& p, cudaStream_t st) : prm(p), s(st) {}
 
-  void alloc_iterates() {
+  void alloc_shared() {
     const int64_t m = P.m, n = P.n;
-    for (int q = 0; q < 2; ++q) {
-      b.X[q] = arena.alloc<T>(n);
-      b.ATY[q] = arena.alloc<T>(n);
-      b.Y[q] = arena.alloc<T>(m);
-      b.AX[q] = arena.alloc<T>(m);
-    }
-    b.Sx = arena.alloc<T>(n);
-    b.SATy = arena.alloc<T>(n);
-    b.Sy = arena.alloc<T>(m);
-    b.SAx = arena.alloc<T>(m);
-    b.c = P.c;
-    b.lc = P.lc;
-    b.uc = P.uc;
-    b.lv = P.lv;
-    b.uv = P.uv;
-    b.m = m;
-    b.n = n;
-    X0 = arena.alloc<T>(n);
-    Y0 = arena.alloc<T>(m);
     Xa = arena.alloc<T>(n);
     ATYa = arena.alloc<T>(n);
     Ya = arena.alloc<T>(m);
     AXa = arena.alloc<T>(m);
-    dst = arena.alloc<DevState>(1);
     g_primal = primal_grid(n);
     g_a = spmv_grid<T>(P.A, kEpiDual);
     g_at = spmv_grid<T>(P.AT, kEpiAverage);
     g_plain_a = spmv_grid<T>(P.A, kEpiPlain);
+    g_plain_at = spmv_grid<T>(P.AT, kEpiPlain);
     g_red = std::max(1, num_sms() * 4);
     part_primal = arena.alloc<double>(g_primal);
     part_dual = arena.alloc<double>(2 * (int64_t)g_a);
@@ -561,38 +602,86 @@ struct Solver {
     dist_out = arena.alloc<double>(2);
   }
 
-  void zero_sums() {
-    PDLP_CUDA_CHECK(cudaMemsetAsync(b.Sx, 0, sizeof(T) * P.n, s));
-    PDLP_CUDA_CHECK(cudaMemsetAsync(b.SATy, 0, sizeof(T) * P.n, s));
+  void alloc_run(Run<T>& r) {
+    const int64_t m = P.m, n = P.n;
+    for (int q = 0; q < 2; ++q) {
+      r.b.X[q] = arena.alloc<T>(n);
+      r.b.ATY[q] = arena.alloc<T>(n);
+      r.b.Y[q] = arena.alloc<T>(m);
+      r.b.AX[q] = arena.alloc<T>(m);
+    }
+    r.b.Sx = arena.alloc<T>(n);
+    r.b.SATy = arena.alloc<T>(n);
+    r.b.Sy = arena.alloc<T>(m);
+    r.b.SAx = arena.alloc<T>(m);
+    r.b.m = m;
+    r.b.n = n;
+    r.X0 = arena.alloc<T>(n);
+    r.Y0 = arena.alloc<T>(m);
+    r.dst = arena.alloc<DevState>(1);
+  }
+
+  void alloc_polishing() {
+    const int64_t m = P.m, n = P.n;
+    alloc_run(pol_run);
+    c_zero = arena.alloc<T>(n);
+    PDLP_CUDA_CHECK(cudaMemsetAsync(c_zero, 0, sizeof(T) * n, s));
+    zlv = arena.alloc<T>(n);
+    zuv = arena.alloc<T>(n);
+    zlc = arena.alloc<T>(m);
+    zuc = arena.alloc<T>(m);
+    k_zero_finite<T><<<vec_grid(n), kThreads, 0, s>>>(P.lv, zlv, n);
+    k_zero_finite<T><<<vec_grid(n), kThreads, 0, s>>>(P.uv, zuv, n);
+    launches += 2;
+    if (m) {
+      k_zero_finite<T><<<vec_grid(m), kThreads, 0, s>>>(P.lc, zlc, m);
+      k_zero_finite<T><<<vec_grid(m), kThreads, 0, s>>>(P.uc, zuc, m);
+      launches += 2;
+    }
+    PDLP_LAUNCH_CHECK();
+    Xk = arena.alloc<T>(n);
+    Xt = arena.alloc<T>(n);
+    ATYt = arena.alloc<T>(n);
+    Yk = arena.alloc<T>(m);
+    Yt = arena.alloc<T>(m);
+    AXt = arena.alloc<T>(m);
+  }
+
+  void zero_sums(Run<T>& r) {
+    PDLP_CUDA_CHECK(cudaMemsetAsync(r.b.Sx, 0, sizeof(T) * P.n, s));
+    PDLP_CUDA_CHECK(cudaMemsetAsync(r.b.SATy, 0, sizeof(T) * P.n, s));
     if (P.m) {
-      PDLP_CUDA_CHECK(cudaMemsetAsync(b.Sy, 0, sizeof(T) * P.m, s));
-      PDLP_CUDA_CHECK(cudaMemsetAsync(b.SAx, 0, sizeof(T) * P.m, s));
+      PDLP_CUDA_CHECK(cudaMemsetAsync(r.b.Sy, 0, sizeof(T) * P.m, s));
+      PDLP_CUDA_CHECK(cudaMemsetAsync(r.b.SAx, 0, sizeof(T) * P.m, s));
     }
   }
 
-  void push_state() {
-    PDLP_CUDA_CHECK(cudaMemcpyAsync(dst, &hs, sizeof(DevState), cudaMemcpyHostToDevice, s));
+  void push_state(Run<T>& r) {
+    PDLP_CUDA_CHECK(cudaMemcpyAsync(r.dst, &r.hs, sizeof(DevState), cudaMemcpyHostToDevice, s));
   }
-  void pull_state() {
-    PDLP_CUDA_CHECK(cudaMemcpyAsync(&hs, dst, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  void pull_state(Run<T>& r) {
+    PDLP_CUDA_CHECK(cudaMemcpyAsync(&r.hs, r.dst, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
     timer.collect();
   }
 
-  PointRef<T> current() const {
-    return PointRef<T>{b.X[hs.cur], b.Y[hs.cur], b.AX[hs.cur], b.ATY[hs.cur]};
+  PointRef<T> current(const Run<T>& r) const {
+    return PointRef<T>{r.b.X[r.hs.cur], r.b.Y[r.hs.cur], r.b.AX[r.hs.cur], r.b.ATY[r.hs.cur]};
   }
   PointRef<T> average() const { return PointRef<T>{Xa, Ya, AXa, ATYa}; }
-  ScaledVecs<T> scaled() const { return ScaledVecs<T>{P.c, P.lc, P.uc, P.lv, P.uv, P.m, P.n}; }
+  static ScaledVecs<T> vecs(const Run<T>& r) {
+    return ScaledVecs<T>{r.b.c, r.b.lc, r.b.uc, r.b.lv, r.b.uv, r.b.m, r.b.n};
+  }
   OrigVecs origv() const {
     return OrigVecs{P.orig.c, P.orig.lc, P.orig.uc, P.orig.lv, P.orig.uv,
                     P.d1,     P.d2,      P.inv_d1,  P.inv_d2};
   }
 
-  double gap(const PointRef<T>& z, double omega) {
+  double gap(const Run<T>& r, const PointRef<T>& z, double omega) {
     auto t0 = Clock::now();
     int nl = 0;
-    const double mu = normalized_gap<T>(z, X0, Y0, omega, scaled(), gsc, s, &nl, &gap_stats);
+    const double mu =
+        normalized_gap<T>(z, r.X0, r.Y0, omega, vecs(r), gsc, s, &nl, &gap_stats);
     launches += nl;
     ms_checks += 1e3 * secs_since(t0);
     return mu;
@@ -610,15 +699,15 @@ struct Solver {
   }
 
   // one step attempt = three launches (see file comment)
-  void launch_slot() {
+  void launch_slot(Run<T>& r) {
     int e0 = timer.begin(s);
-    launch_primal<T>(b, dst, part_primal, g_primal, s);
+    launch_primal<T>(r.b, r.dst, part_primal, g_primal, s);
     timer.end(e0, 2, s);
     int e1 = timer.begin(s);
-    launch_spmv_dual<T>(P.A, b, dst, part_primal, g_primal, part_dual, counters, g_a, s);
+    launch_spmv_dual<T>(P.A, r.b, r.dst, part_primal, g_primal, part_dual, counters, g_a, s);
     timer.end(e1, 0, s);
     int e2 = timer.begin(s);
-    launch_spmv_avg<T>(P.AT, b, dst, g_at, s);
+    launch_spmv_avg<T>(P.AT, r.b, r.dst, g_at, s);
     timer.end(e2, 1, s);
     launches += 3;
   }
@@ -638,120 +727,115 @@ struct Solver {
     return j;
   }
 
-  int run(const Inputs& in, double* x_out, double* y_out, pdlp_stats* st) {
-    const auto t_start = Clock::now();
-    DevInputs d = stage_inputs(arena, in, s);
-    validate(arena, in, d, s);
-    build_problem<T>(arena, in, d, prm.ruiz_iters, prm.pc_alpha, P, s);
-    launches += P.launches;
-    alloc_iterates();
+  // Starts run r on the LP with scaled vectors (c, lc, uc, lv, uv) from (x_start,
+  // y_start) (device vectors of the renumbered LP; null = 0), or from z^{0,0} =
+  // (proj_X(0), 0) when both are null, with primal weight omega and step eta_hat.
+  void start_run(Run<T>& r, const T* x_start, const T* y_start, double omega, double eta_hat,
+                 int64_t max_iters, int goal, const T* c, const T* lc, const T* uc,
+                 const T* lv, const T* uv) {
     const int64_t m = P.m, n = P.n;
-
-    // z^{0,0} = (proj_X(0), 0)
-    k_init_point<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(P.lv, P.uv, b.X[0], b.Y[0],
-                                                                   b.ATY[0], X0, Y0, m, n);
-    PDLP_LAUNCH_CHECK();
-    launch_spmv_plain<T>(P.A, b.X[0], b.AX[0], g_plain_a, s);
-    launches += 2;
-    zero_sums();
-    const double eta0 = P.max_abs > 0.0 ? 1.0 / P.max_abs : 1.0;
-    const double omega0 = (P.c_norm_s > 0.0 && P.b_norm_s > 0.0) ? P.c_norm_s / P.b_norm_s : 1.0;
-    std::memset(&hs, 0, sizeof(hs));
-    hs.cur = 0;
-    hs.eta = eta0;
-    hs.eta_hat = eta0;
-    hs.omega = omega0;
-    hs.max_retries = prm.max_step_retries;
-    push_state();
-    PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
-    const double t_setup = secs_since(t_start);
-    const auto t_solve0 = Clock::now();
-    timer.on = prm.profile != 0;
-
-    const int64_t period = std::max(1, prm.check_period);
-    const int64_t trace_iters = (prm.trace_out && prm.trace_iters > 0) ? prm.trace_iters : 0;
-    const int64_t rec_len = PDLP_TRACE_HEADER + n + m;
-    std::vector<T> hx, hy;
-    std::vector<int32_t> hperm_c, hperm_r;
-    if (trace_iters) {
-      hperm_c.resize(n);
-      hperm_r.resize(m);
-      PDLP_CUDA_CHECK(cudaMemcpyAsync(hperm_c.data(), P.perm_c, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
-      if (m) PDLP_CUDA_CHECK(cudaMemcpyAsync(hperm_r.data(), P.perm_r, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s));
-      PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+    r.b.c = c;
+    r.b.lc = lc;
+    r.b.uc = uc;
+    r.b.lv = lv;
+    r.b.uv = uv;
+    if (!x_start && !y_start) {
+      k_init_point<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(
+          lv, uv, r.b.X[0], r.b.Y[0], r.b.ATY[0], r.X0, r.Y0, m, n);
+      PDLP_LAUNCH_CHECK();
+      launches++;
+    } else {
+      k_start_point<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(
+          x_start, y_start, r.b.X[0], r.b.Y[0], r.X0, r.Y0, m, n);
+      PDLP_LAUNCH_CHECK();
+      launch_spmv_plain<T>(P.AT, r.b.Y[0], r.b.ATY[0], g_plain_at, s);
+      launches += 2;
     }
+    launch_spmv_plain<T>(P.A, r.b.X[0], r.b.AX[0], g_plain_a, s);
+    launches++;
+    zero_sums(r);
+    std::memset(&r.hs, 0, sizeof(r.hs));
+    r.hs.cur = 0;
+    r.hs.eta = eta_hat;
+    r.hs.eta_hat = eta_hat;
+    r.hs.omega = omega;
+    r.hs.max_retries = prm.max_step_retries;
+    push_state(r);
+    r.goal = goal;
+    r.max_iters = max_iters;
+    r.started = false;
+    r.have_mu_ref = false;
+    r.mu_ref = 0.0;
+    r.mu_c_prev = INFINITY;
+    r.k = r.t = r.attempts_at_last = 0;
+    r.restarts[0] = r.restarts[1] = r.restarts[2] = 0;
+  }
 
-    int status = -100;
-    int64_t restarts[3] = {0, 0, 0};
-    bool have_mu_ref = false;
-    double mu_ref = 0.0, mu_c_prev = INFINITY;
-    PointRef<T> out_pt = current();
-    KktResult out_k{};
-
-    // termination test on z^{0,0} before the first step
-    out_k = kkt(current());
-    if (converged(out_k, prm)) status = PDLP_OPTIMAL;
-
-    int64_t k = 0, t = 0, attempts_at_last = 0;
-    while (status == -100) {
-      const int64_t next_check = (k / period + 1) * period;
-      int64_t target = std::min(next_check, prm.max_iters);
-      const int64_t j_art = steps_to_artificial(k, t);
-      if (k + j_art < target) target = k + j_art;
+  // Advances run r (Algorithm 1 with device-side Algorithm 2 steps, the restart scheme
+  // of Sec. 3 and Algorithm 3) until its goal is met on a restart candidate, its
+  // iteration cap or the time limit is reached, a step fails, or -- pause_at >= 0 --
+  // pause_at iterations are complete (with that iteration's check and restart done).
+  // out_pt / out_k receive the point to return and its KKT measures (not for a pause).
+  RunOutcome advance(Run<T>& r, int64_t pause_at, PointRef<T>& out_pt, KktResult& out_k) {
+    const int64_t m = P.m, n = P.n;
+    const int64_t period = std::max(1, prm.check_period);
+    const int64_t trace_iters =
+        (r.trace && prm.trace_out && prm.trace_iters > 0) ? prm.trace_iters : 0;
+    const int64_t rec_len = PDLP_TRACE_HEADER + n + m;
+    if (!r.started) {
+      r.started = true;
+      // termination test on the start point before the first step
+      out_k = kkt(current(r));
+      if (goal_met(out_k, prm, r.goal)) {
+        out_pt = current(r);
+        return kRunDone;
+      }
+    }
+    for (;;) {
+      if (pause_at >= 0 && r.k >= pause_at) return kRunPaused;
+      const int64_t next_check = (r.k / period + 1) * period;
+      int64_t target = std::min(next_check, r.max_iters);
+      if (pause_at >= 0) target = std::min(target, pause_at);
+      const int64_t j_art = steps_to_artificial(r.k, r.t);
+      if (r.k + j_art < target) target = r.k + j_art;
       // launch attempts until `target` accepted iterations (rejections need more)
       bool error = false;
-      while (k < target) {
-        const int64_t need = (trace_iters > k) ? 1 : (target - k);
-        for (int64_t q = 0; q < need; ++q) launch_slot();
-        const double omega_used = hs.omega;
-        pull_state();
-        if (hs.error) {
+      while (r.k < target) {
+        const int64_t need = (trace_iters > r.k) ? 1 : (target - r.k);
+        for (int64_t q = 0; q < need; ++q) launch_slot(r);
+        const double omega_used = r.hs.omega;
+        pull_state(r);
+        if (r.hs.error) {
           error = true;
           break;
         }
-        if (trace_iters > k && hs.k > k) {
-          // record the accepted iteration hs.k (one slot per pull in trace mode)
-          double* rec = prm.trace_out + (size_t)k * rec_len;
-          rec[0] = (double)hs.k;
-          rec[1] = hs.eta_acc;
-          rec[2] = omega_used;
-          rec[3] = hs.eta_hat;
-          rec[4] = (double)(hs.attempts - attempts_at_last);
-          rec[5] = 0.0;
-          rec[6] = NAN;
-          rec[7] = NAN;
-          hx.resize(n);
-          hy.resize(m);
-          PDLP_CUDA_CHECK(cudaMemcpyAsync(hx.data(), b.X[hs.cur], sizeof(T) * n, cudaMemcpyDeviceToHost, s));
-          if (m) PDLP_CUDA_CHECK(cudaMemcpyAsync(hy.data(), b.Y[hs.cur], sizeof(T) * m, cudaMemcpyDeviceToHost, s));
-          PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
-          for (int64_t j = 0; j < n; ++j) rec[PDLP_TRACE_HEADER + hperm_c[j]] = (double)hx[j];
-          for (int64_t i = 0; i < m; ++i) rec[PDLP_TRACE_HEADER + n + hperm_r[i]] = (double)hy[i];
-        }
-        if (hs.k > k) attempts_at_last = hs.attempts;
-        k = hs.k;
-        t = hs.t;
+        if (trace_iters > r.k && r.hs.k > r.k) record_trace(r, omega_used, rec_len);
+        if (r.hs.k > r.k) r.attempts_at_last = r.hs.attempts;
+        r.k = r.hs.k;
+        r.t = r.hs.t;
       }
       if (error) {
-        status = PDLP_NUMERICAL_ERROR;
-        out_pt = current();
+        out_pt = current(r);
         out_k = kkt(out_pt);
-        break;
+        return kRunError;
       }
-      double* rec = (trace_iters >= k && k >= 1) ? prm.trace_out + (size_t)(k - 1) * rec_len : nullptr;
+      const int64_t k = r.k, t = r.t;
+      double* rec =
+          (trace_iters >= k && k >= 1) ? prm.trace_out + (size_t)(k - 1) * rec_len : nullptr;
       const bool is_check = (k % period) == 0;
       const bool is_art = (double)t >= prm.beta_art * (double)k;
-      const bool is_limit = k >= prm.max_iters;
+      const bool is_limit = k >= r.max_iters;
       if (!(is_check || is_art || is_limit)) continue;
       // GetRestartCandidate: current vs average since the restart
-      launch_average<T>(b.Sx, b.Sy, b.SAx, b.SATy, 1.0 / hs.W, P.lv, P.uv, Xa, Ya, AXa, ATYa, m, n, s);
+      launch_average<T>(r.b.Sx, r.b.Sy, r.b.SAx, r.b.SATy, 1.0 / r.hs.W, r.b.lv, r.b.uv, Xa, Ya,
+                        AXa, ATYa, m, n, s);
       launches++;
-      const double omega = hs.omega;
-      const double mu_cur = gap(current(), omega);
-      const double mu_avg = gap(average(), omega);
+      const double omega = r.hs.omega;
+      const double mu_cur = gap(r, current(r), omega);
+      const double mu_avg = gap(r, average(), omega);
       const bool cand_avg = !(mu_cur < mu_avg);
       const double mu_c = cand_avg ? mu_avg : mu_cur;
-      const PointRef<T> cand = cand_avg ? average() : current();
+      const PointRef<T> cand = cand_avg ? average() : current(r);
       if (rec) {
         rec[6] = mu_cur;
         rec[7] = mu_avg;
@@ -759,67 +843,279 @@ struct Solver {
       if (is_check || is_limit) {
         out_k = kkt(cand);
         if (prm.verbose)
-          std::fprintf(stderr, "pdlp: k=%lld rel_kkt=%.3e pobj=%.10e omega=%.3e eta=%.3e\n",
-                       (long long)k, out_k.rel_kkt, out_k.pobj, omega, hs.eta_hat);
-        if (converged(out_k, prm)) {
-          status = PDLP_OPTIMAL;
+          std::fprintf(stderr, "pdlp: goal=%d k=%lld rel_kkt=%.3e pobj=%.10e omega=%.3e eta=%.3e\n",
+                       r.goal, (long long)k, out_k.rel_kkt, out_k.pobj, omega, r.hs.eta_hat);
+        if (goal_met(out_k, prm, r.goal)) {
           out_pt = cand;
-          break;
+          return kRunDone;
         }
         if (is_limit) {
-          status = PDLP_ITERATION_LIMIT;
           out_pt = cand;
-          break;
+          return kRunLimit;
         }
         if (secs_since(t_solve0) > prm.time_limit_s) {
-          status = PDLP_TIME_LIMIT;
           out_pt = cand;
-          break;
+          return kRunTime;
         }
       }
       int kind = 0;
-      if (is_check && have_mu_ref) {
-        if (mu_c <= prm.beta_suff * mu_ref)
+      if (is_check && r.have_mu_ref) {
+        if (mu_c <= prm.beta_suff * r.mu_ref)
           kind = 1;
-        else if (mu_c <= prm.beta_nec * mu_ref && mu_c > mu_c_prev)
+        else if (mu_c <= prm.beta_nec * r.mu_ref && mu_c > r.mu_c_prev)
           kind = 2;
       }
       if (kind == 0 && is_art) kind = 3;
-      if (is_check) mu_c_prev = mu_c;
+      if (is_check) r.mu_c_prev = mu_c;
       if (kind == 0) continue;
       // restart the outer loop at the candidate
-      restarts[kind - 1]++;
+      r.restarts[kind - 1]++;
       if (rec) rec[5] = (double)kind;
-      const int cur = hs.cur;
+      const int cur = r.hs.cur;
       if (cand_avg) {
-        k_copy2<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(Xa, b.X[cur], n, Ya, b.Y[cur], m);
-        k_copy2<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(ATYa, b.ATY[cur], n, AXa, b.AX[cur], m);
+        k_copy2<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(Xa, r.b.X[cur], n, Ya, r.b.Y[cur], m);
+        k_copy2<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(ATYa, r.b.ATY[cur], n, AXa, r.b.AX[cur], m);
         PDLP_LAUNCH_CHECK();
         launches += 2;
       }
       // Algorithm 3
-      launch_dist2<T>(b.X[cur], X0, b.Y[cur], Y0, m, n, dist_part, counters + 3, dist_out, g_red, s);
+      launch_dist2<T>(r.b.X[cur], r.X0, r.b.Y[cur], r.Y0, m, n, dist_part, counters + 3, dist_out,
+                      g_red, s);
       launches++;
       double d2h[2];
       PDLP_CUDA_CHECK(cudaMemcpyAsync(d2h, dist_out, sizeof(d2h), cudaMemcpyDeviceToHost, s));
       PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
       const double dx = std::sqrt(d2h[0]), dy = std::sqrt(d2h[1]);
-      double om = hs.omega;
+      double om = r.hs.omega;
       if (prm.eps_zero < dx && dx < 1.0 / prm.eps_zero && prm.eps_zero < dy && dy < 1.0 / prm.eps_zero)
         om = std::exp(prm.theta * std::log(dy / dx) + (1.0 - prm.theta) * std::log(om));
-      mu_ref = gap(current(), om);
-      have_mu_ref = true;
-      k_copy2<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(b.X[cur], X0, n, b.Y[cur], Y0, m);
+      r.mu_ref = gap(r, current(r), om);
+      r.have_mu_ref = true;
+      k_copy2<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(r.b.X[cur], r.X0, n, r.b.Y[cur], r.Y0, m);
       PDLP_LAUNCH_CHECK();
       launches++;
-      zero_sums();
-      mu_c_prev = INFINITY;
-      hs.omega = om;
-      hs.W = 0.0;
-      hs.t = 0;
-      t = 0;
-      push_state();
+      zero_sums(r);
+      r.mu_c_prev = INFINITY;
+      r.hs.omega = om;
+      r.hs.W = 0.0;
+      r.hs.t = 0;
+      r.t = 0;
+      push_state(r);
     }
+  }
+
+  // trace record of accepted iteration r.hs.k (one slot per pull in trace mode)
+  std::vector<T> hx, hy;
+  std::vector<int32_t> hperm_c, hperm_r;
+  void record_trace(Run<T>& r, double omega_used, int64_t rec_len) {
+    const int64_t m = P.m, n = P.n;
+    double* rec = prm.trace_out + (size_t)r.k * rec_len;
+    rec[0] = (double)r.hs.k;
+    rec[1] = r.hs.eta_acc;
+    rec[2] = omega_used;
+    rec[3] = r.hs.eta_hat;
+    rec[4] = (double)(r.hs.attempts - r.attempts_at_last);
+    rec[5] = 0.0;
+    rec[6] = NAN;
+    rec[7] = NAN;
+    if (hperm_c.empty() && n) {
+      hperm_c.resize(n);
+      hperm_r.resize(m);
+      PDLP_CUDA_CHECK(cudaMemcpyAsync(hperm_c.data(), P.perm_c, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+      if (m) PDLP_CUDA_CHECK(cudaMemcpyAsync(hperm_r.data(), P.perm_r, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s));
+    }
+    hx.resize(n);
+    hy.resize(m);
+    PDLP_CUDA_CHECK(cudaMemcpyAsync(hx.data(), r.b.X[r.hs.cur], sizeof(T) * n, cudaMemcpyDeviceToHost, s));
+    if (m) PDLP_CUDA_CHECK(cudaMemcpyAsync(hy.data(), r.b.Y[r.hs.cur], sizeof(T) * m, cudaMemcpyDeviceToHost, s));
+    PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+    for (int64_t j = 0; j < n; ++j) rec[PDLP_TRACE_HEADER + hperm_c[j]] = (double)hx[j];
+    for (int64_t i = 0; i < m; ++i) rec[PDLP_TRACE_HEADER + n + hperm_r[i]] = (double)hy[i];
+  }
+
+  // status of a finished run
+  static int status_of(RunOutcome o) {
+    switch (o) {
+      case kRunDone: return PDLP_OPTIMAL;
+      case kRunLimit: return PDLP_ITERATION_LIMIT;
+      case kRunTime: return PDLP_TIME_LIMIT;
+      default: return PDLP_NUMERICAL_ERROR;
+    }
+  }
+
+  struct PolishTotals {
+    int64_t pauses = 0, primal_iters = 0, dual_iters = 0, accepted_k = 0;
+  } pol;
+
+  // The two phases of Algorithm 4 from (x^k, y^k) = (Xk, Yk), with primal weight omega
+  // and step eta, each for at most `budget` iterations.  Returns 1 when the polished
+  // pair meets the termination criteria (out_pt / out_k set to it), 2 when the time
+  // limit ran out, 0 otherwise.  `row` (may be null) receives the phases' log entries.
+  int polish_phases(int64_t budget, double omega, double eta, double* row, PointRef<T>& out_pt,
+                    KktResult& out_k) {
+    const int64_t m = P.m, n = P.n;
+    // primal feasibility problem (objective 0) from (x^k, 0)
+    start_run(pol_run, Xk, nullptr, omega, eta, budget, kGoalPrimalFeasible, c_zero, P.lc, P.uc,
+              P.lv, P.uv);
+    PointRef<T> pp;
+    KktResult kpp;
+    const RunOutcome op = advance(pol_run, -1, pp, kpp);
+    pol.primal_iters += pol_run.k;
+    if (row) {
+      row[2] = (double)pol_run.k;
+      row[3] = op == kRunDone ? 1.0 : 0.0;
+    }
+    if (op == kRunTime) return 2;
+    if (op != kRunDone) return 0;
+    k_copy2<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(pp.x, Xt, n, pp.ax, AXt, m);
+    PDLP_LAUNCH_CHECK();
+    launches++;
+    // dual feasibility problem (finite bounds set to 0) from (0, y^k)
+    start_run(pol_run, nullptr, Yk, omega, eta, budget, kGoalDualFeasible, P.c, zlc, zuc, zlv, zuv);
+    PointRef<T> pd;
+    KktResult kpd;
+    const RunOutcome od = advance(pol_run, -1, pd, kpd);
+    pol.dual_iters += pol_run.k;
+    if (row) {
+      row[4] = (double)pol_run.k;
+      row[5] = od == kRunDone ? 1.0 : 0.0;
+    }
+    if (od == kRunTime) return 2;
+    k_copy2<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(pd.aty, ATYt, n, pd.y, Yt, m);
+    PDLP_LAUNCH_CHECK();
+    launches++;
+    const PointRef<T> pair{Xt, Yt, AXt, ATYt};
+    const KktResult kf = kkt(pair);
+    if (!converged(kf, prm)) return 0;
+    if (row) row[6] = 1.0;
+    out_pt = pair;
+    out_k = kf;
+    return 1;
+  }
+
+  // FP32 bulk: the phases run in FP64 on a second, FP64 copy of the preconditioned
+  // problem (same scaling and numbering, from the unscaled staged inputs din_), built
+  // at the first pause that needs it.
+  const Inputs* in_ = nullptr;
+  DevInputs din_{};
+  std::unique_ptr<Solver<double>> aux64;
+  bool out_from_aux = false;
+  PointRef<double> aux_pt{};
+
+  void prepare_phases(const Inputs& in, const DevInputs& d, Clock::time_point t0) {
+    build_problem<T>(arena, in, d, prm.ruiz_iters, prm.pc_alpha, P, s);
+    launches += P.launches;
+    alloc_shared();
+    alloc_polishing();
+    t_solve0 = t0;
+  }
+
+  // Algorithm 4: normal PDLP (main_run) with pauses at k = 100, 200, 400, ...
+  int solve_polished(PointRef<T>& out_pt, KktResult& out_k) {
+    const int64_t m = P.m, n = P.n;
+    for (int64_t kp = 100;; kp *= 2) {
+      const RunOutcome o = advance(main_run, kp, out_pt, out_k);
+      if (o != kRunPaused) return status_of(o);
+      // (x^k, y^k): the average since the last restart (right after a restart, the
+      // restart point)
+      PointRef<T> zk = current(main_run);
+      if (main_run.hs.W != 0.0) {
+        launch_average<T>(main_run.b.Sx, main_run.b.Sy, main_run.b.SAx, main_run.b.SATy,
+                          1.0 / main_run.hs.W, P.lv, P.uv, Xa, Ya, AXa, ATYa, m, n, s);
+        launches++;
+        zk = average();
+      }
+      const KktResult kz = kkt(zk);
+      double* row = nullptr;
+      if (prm.polish_log && pol.pauses < prm.polish_log_cap) {
+        row = prm.polish_log + (size_t)pol.pauses * PDLP_POLISH_LOG_COLS;
+        for (int q = 0; q < PDLP_POLISH_LOG_COLS; ++q) row[q] = 0.0;
+        row[0] = (double)kp;
+        row[1] = kz.paper_gap;
+      }
+      pol.pauses++;
+      if (!(kz.paper_gap < prm.eps_rel_gap)) continue;
+      const double omega = main_run.hs.omega, eta = main_run.hs.eta_hat;
+      const int64_t budget = kp / 8;
+      int r;
+      if constexpr (std::is_same<T, double>::value) {
+        k_copy2<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(zk.x, Xk, n, zk.y, Yk, m);
+        PDLP_LAUNCH_CHECK();
+        launches++;
+        r = polish_phases(budget, omega, eta, row, out_pt, out_k);
+      } else {
+        if (!aux64) {
+          aux64.reset(new Solver<double>(prm, s));
+          aux64->prepare_phases(*in_, din_, t_solve0);
+        }
+        k_to_double2<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(zk.x, aux64->Xk, n, zk.y,
+                                                                      aux64->Yk, m);
+        PDLP_LAUNCH_CHECK();
+        launches++;
+        r = aux64->polish_phases(budget, omega, eta, row, aux_pt, out_k);
+        out_from_aux = r == 1;
+      }
+      if (r == 2) {
+        out_from_aux = false;
+        out_pt = current(main_run);
+        out_k = kkt(out_pt);
+        return PDLP_TIME_LIMIT;
+      }
+      if (r == 1) {
+        pol.accepted_k = kp;
+        return PDLP_OPTIMAL;
+      }
+    }
+  }
+
+  // x = D2 x~, y = D1 y~ of a point of problem Q, into the caller's numbering
+  template <class U>
+  void emit(const Problem<U>& Q, const PointRef<U>& pt, double* xo, double* yo) {
+    const int64_t m = Q.m, n = Q.n;
+    k_unscale<U><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(
+        pt.x, pt.y, Q.d1, Q.d2, Q.orig.lv, Q.orig.uv, Q.perm_r, Q.perm_c, xo, yo, m, n);
+    PDLP_LAUNCH_CHECK();
+    launches++;
+  }
+
+  int run(const Inputs& in, double* x_out, double* y_out, pdlp_stats* st) {
+    const auto t_start = Clock::now();
+    DevInputs d = stage_inputs(arena, in, s);
+    validate(arena, in, d, s);
+    in_ = &in;
+    din_ = d;
+    if (prm.feasibility_polishing && !std::is_same<T, double>::value && in.nnz) {
+      // build_problem scales the staged values in place; the FP64 phase problem is
+      // built later from an unscaled copy
+      double* v = arena.alloc<double>(in.nnz);
+      PDLP_CUDA_CHECK(cudaMemcpyAsync(v, d.val, sizeof(double) * in.nnz, cudaMemcpyDeviceToDevice, s));
+      din_.val = v;
+    }
+    build_problem<T>(arena, in, d, prm.ruiz_iters, prm.pc_alpha, P, s);
+    launches += P.launches;
+    alloc_shared();
+    alloc_run(main_run);
+    if (prm.feasibility_polishing && std::is_same<T, double>::value) alloc_polishing();
+    const int64_t m = P.m, n = P.n;
+
+    const double eta0 = P.max_abs > 0.0 ? 1.0 / P.max_abs : 1.0;
+    const double omega0 = (P.c_norm_s > 0.0 && P.b_norm_s > 0.0) ? P.c_norm_s / P.b_norm_s : 1.0;
+    // z^{0,0} = (proj_X(0), 0)
+    start_run(main_run, nullptr, nullptr, omega0, eta0, prm.max_iters, kGoalOptimal, P.c, P.lc,
+              P.uc, P.lv, P.uv);
+    main_run.trace = true;
+    PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+    const double t_setup = secs_since(t_start);
+    t_solve0 = Clock::now();
+    timer.on = prm.profile != 0;
+
+    PointRef<T> out_pt = current(main_run);
+    KktResult out_k{};
+    int status;
+    if (prm.feasibility_polishing)
+      status = solve_polished(out_pt, out_k);
+    else
+      status = status_of(advance(main_run, -1, out_pt, out_k));
 
     // output: the returned point, unscaled
     double* xo = x_out;
@@ -832,10 +1128,10 @@ struct Solver {
       xo = dx_out;
       yo = dy_out;
     }
-    k_unscale<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(
-        out_pt.x, out_pt.y, P.d1, P.d2, P.orig.lv, P.orig.uv, P.perm_r, P.perm_c, xo, yo, m, n);
-    PDLP_LAUNCH_CHECK();
-    launches++;
+    if (out_from_aux)
+      emit<double>(aux64->P, aux_pt, xo, yo);
+    else
+      emit<T>(P, out_pt, xo, yo);
     if (!in.on_device) {
       PDLP_CUDA_CHECK(cudaMemcpyAsync(x_out, dx_out, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
       if (m) PDLP_CUDA_CHECK(cudaMemcpyAsync(y_out, dy_out, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
@@ -843,12 +1139,13 @@ struct Solver {
     PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
     timer.collect();
     if (st) {
+      const DevState& hs = main_run.hs;
       std::memset(st, 0, sizeof(*st));
       st->status = status;
       st->iterations = hs.k;
       st->attempts = hs.attempts;
       st->rejected_steps = hs.rejected;
-      for (int q = 0; q < 3; ++q) st->restarts[q] = restarts[q];
+      for (int q = 0; q < 3; ++q) st->restarts[q] = main_run.restarts[q];
       st->kkt_passes = 0.5 * (double)(hs.attempts + hs.k);
       st->rel_kkt = out_k.rel_kkt;
       st->rel_primal = out_k.rel_primal;
@@ -872,15 +1169,25 @@ struct Solver {
       st->ms_checks = ms_checks;
       st->launches_spmv_a = timer.count[0];
       st->launches_spmv_at = timer.count[1];
-      st->kernel_launches = launches;
+      st->kernel_launches = launches + (aux64 ? aux64->launches : 0);
       const double v = (double)sizeof(T);
       st->gap_evals = gap_stats.evals;
       st->gap_fallbacks = gap_stats.fallbacks;
       st->gap_failures = gap_stats.failures;
       if (gap_stats.failures) set_last_error(gap_stats.last_failure);
+      if (aux64) {
+        st->gap_evals += aux64->gap_stats.evals;
+        st->gap_fallbacks += aux64->gap_stats.fallbacks;
+        st->gap_failures += aux64->gap_stats.failures;
+        if (aux64->gap_stats.failures) set_last_error(aux64->gap_stats.last_failure);
+      }
       st->bytes_spmv_a = (double)(m + 1) * 8 + (double)P.nnz * (4 + v) + (double)n * v + 6.0 * m * v;
       st->bytes_spmv_at = (double)(n + 1) * 8 + (double)P.nnz * (4 + v) + (double)m * v +
                           6.0 * (double)n * v + 6.0 * (double)m * v;
+      st->polish_pauses = pol.pauses;
+      st->polish_primal_iters = pol.primal_iters + (aux64 ? aux64->pol.primal_iters : 0);
+      st->polish_dual_iters = pol.dual_iters + (aux64 ? aux64->pol.dual_iters : 0);
+      st->polish_accepted_k = pol.accepted_k;
     }
     return status;
   }
@@ -975,6 +1282,9 @@ void pdlp_params_default(pdlp_params* p) {
   p->trace_out = nullptr;
   p->profile = 0;
   p->verbose = 0;
+  p->feasibility_polishing = 0;
+  p->polish_log_cap = 0;
+  p->polish_log = nullptr;
 }
 
 const char* pdlp_last_error(void) { return g_last_error; }

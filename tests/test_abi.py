@@ -81,3 +81,18 @@ def test_params_default_values(lib):
     assert p.check_period == 64 and p.beta_suff == 0.1 and p.beta_nec == 0.9
     assert p.beta_art == 0.5 and p.theta == 0.5 and p.eps_zero == 1e-10
     assert p.precision == 0 and p.inputs_on_device == 0
+
+
+def test_binding_constants_match_header(lib):
+    from paper_2501_07018_gb300 import binding
+
+    defs = dict(re.findall(r"#define\s+(PDLP_\w+)\s+\(?(-?\d+)\)?", open(HEADER).read()))
+    assert int(defs["PDLP_TRACE_HEADER"]) == binding.TRACE_HEADER
+    assert int(defs["PDLP_POLISH_LOG_COLS"]) == binding.POLISH_LOG_COLS
+    assert int(defs["PDLP_FP32_BULK"]) == binding.FP32_BULK and int(defs["PDLP_FP64"]) == binding.FP64
+    for code, name in binding.STATUS_NAMES.items():
+        key = {"INVALID_ARGUMENT": "PDLP_INVALID_ARGUMENT", "OUT_OF_MEMORY": "PDLP_OUT_OF_MEMORY",
+               "CUDA_ERROR": "PDLP_CUDA_ERROR"}.get(name, "PDLP_" + name)
+        assert int(defs[key]) == code, name
+    p = binding.default_params()
+    assert p.feasibility_polishing == 0 and p.polish_log_cap == 0 and not p.polish_log
