@@ -1,13 +1,25 @@
 """Feasibility polishing (Sec. 5, Algorithm 4) on the CUDA path against the oracle.
 
-The pause schedule and each phase's outcome (iterations, success) must be the
-oracle's exactly: they are integer decisions taken on quantities that agree to
-about 1e-10 relative.  The returned pair must meet the paper's criteria (l_inf
-residuals <= 1e-8, relative gap of Eq. (8) <= 1e-2) as measured by the oracle's
-FP64 definitions, and its objective must agree with the oracle's to 1e-6 relative
-(the tolerance of the plain full-solve parity test)."""
+PDLP's trajectory is sensitive to rounding: on the 200 x 400 LP a one-ulp change of
+one objective entry changes the oracle's own iterates by ~2e-11 after 100
+iterations, ~2e-8 after 200, ~5e-7 after 300 and ~1e-2 after 500 (the adaptive step
+of Algorithm 2 feeds every difference back into the next step), and the GPU path
+departs from the oracle at the same rate.  So:
+
+* trajectory parity (pause schedule, each phase's iteration count and outcome, the
+  gaps at the pauses, the returned point) is tested where the trajectories still
+  agree: runs that end right after the pause at k = 200;
+* full polished solves to the paper's criteria are tested on their results: the
+  returned pair meets the criteria (l_inf residuals <= 1e-8, relative gap of Eq. (8)
+  <= 1e-2) as measured by the oracle's FP64 definitions, the schedule has the
+  structure of Algorithm 4, and the returned objectives bracket the optimum that
+  HiGHS computes (weak duality)."""
+import dataclasses
+
 import numpy as np
 import pytest
+import scipy.optimize as so
+import scipy.sparse as sp
 
 import lpgen
 from oracle import pdlp_oracle as O
@@ -17,6 +29,8 @@ from tests import lp_helpers as H
 pytestmark = pytest.mark.gpu
 
 CRIT = dict(termination_mode=1, eps_abs_feas=1e-8, eps_rel_gap=1e-2, max_iters=30000)
+EARLY = dict(termination_mode=1, eps_abs_feas=1e-2, eps_rel_gap=1e-1, max_iters=201)
+LOG_KEYS = ("k", "primal_iters", "primal_ok", "dual_iters", "dual_ok", "accepted")
 
 
 @pytest.fixture(scope="module")
@@ -40,54 +54,116 @@ def _instance(name):
         return H.lp_with_feasible_pair(np.random.default_rng(21), 300, 500, density=0.05)[0]
     if name == "edge":
         return GH.edge_instance()
-    return lpgen.config1(scale=0.002)
+    return lpgen.config1(scale=0.0005)  # 1000 x 2500, the bench recipe (HiGHS in ~1 s)
+
+
+def _highs_sparse(inst):
+    """Optimal value by scipy's HiGHS on the same LP (rows split into equalities and
+    one-sided inequalities)."""
+    A = inst.scipy_csr()
+    eq = inst.lc == inst.uc
+    up = ~eq & np.isfinite(inst.uc)
+    lo = ~eq & np.isfinite(inst.lc)
+    A_ub = sp.vstack([A[up], -A[lo]]).tocsr()
+    b_ub = np.concatenate([inst.uc[up], -inst.lc[lo]])
+    bounds = [(None if not np.isfinite(l) else l, None if not np.isfinite(u) else u)
+              for l, u in zip(inst.lv, inst.uv)]
+    r = so.linprog(inst.c, A_ub=A_ub if A_ub.shape[0] else None, b_ub=b_ub if b_ub.size else None,
+                   A_eq=A[eq] if eq.any() else None, b_eq=inst.lc[eq] if eq.any() else None,
+                   bounds=bounds, method="highs")
+    assert r.status == 0
+    return r.fun
+
+
+@pytest.mark.parametrize("name", ["config0", "mixed_bounds", "edge"])
+def test_polishing_trajectory_parity(pkg, name):
+    """Runs ending right after the pause at k = 200 (loose criteria, so that phases run
+    at the pauses k = 100 and 200): identical schedule and phase outcomes, gaps at the
+    pauses to 1e-5 relative, and the returned point within 100 times the oracle's own
+    sensitivity to a one-ulp change of one objective entry (worst of three entries) at
+    the same horizon -- measured here, e.g. 8e-8 on the 200 x 400 LP, 3e-6 on the edge
+    LP -- since both sides round differently in every reduction."""
+    inst = _instance(name)
+    prm = O.Params(feasibility_polishing=True, **EARLY)
+    lp = O.precondition(inst)
+    ref = O.solve(inst, prm, lp=lp)
+    sens = 0.0
+    for j in range(3):
+        lp_j = dataclasses.replace(lp, c=lp.c.copy())
+        lp_j.c[j] = np.nextafter(lp_j.c[j], np.inf)
+        pert = O.solve(inst, prm, lp=lp_j)
+        for u, v in ((pert.x, ref.x), (pert.y, ref.y)):
+            sens = max(sens, float(np.max(np.abs(u - v) / np.maximum(1.0, np.abs(v)))))
+    tol = max(1e-9, 100.0 * sens)
+    got = pkg.solve_instance(inst, feasibility_polishing=1, **EARLY)
+    lg, lr = got.stats["polish"], ref.stats["polish"]
+    print(name, [tuple(e[k] for k in LOG_KEYS) for e in lg])
+    assert got.status == ref.status
+    assert len(lg) == len(lr) == got.stats["polish_pauses"] >= 2
+    assert any(e["primal_iters"] for e in lr)
+    for a, b in zip(lg, lr):
+        assert tuple(a[k] for k in LOG_KEYS) == tuple(b[k] for k in LOG_KEYS), (a, b)
+        assert abs(a["paper_gap"] - b["paper_gap"]) <= 1e-5 * b["paper_gap"]
+    assert got.stats["iterations"] == ref.stats["iterations"]
+    assert got.stats["polish_primal_iters"] == ref.stats["polish_primal_iters"]
+    assert got.stats["polish_dual_iters"] == ref.stats["polish_dual_iters"]
+    ex = np.max(np.abs(got.x - ref.x) / np.maximum(1.0, np.abs(ref.x)))
+    ey = np.max(np.abs(got.y - ref.y) / np.maximum(1.0, np.abs(ref.y)))
+    print(name, "status", got.status, "x err", ex, "y err", ey, "tol", tol)
+    assert ex <= tol and ey <= tol
+    again = pkg.solve_instance(inst, feasibility_polishing=1, **EARLY)
+    assert np.array_equal(again.x, got.x) and np.array_equal(again.y, got.y)
 
 
 @pytest.mark.parametrize("name", ["config0", "mixed_bounds", "edge", "powerlaw"])
-def test_polished_solve_matches_oracle(pkg, name):
+def test_polished_solve_meets_paper_criteria(pkg, name):
     inst = _instance(name)
-    ref = O.solve(inst, O.Params(feasibility_polishing=True, **CRIT))
     got = pkg.solve_instance(inst, device=True, feasibility_polishing=1, **CRIT)
-    assert ref.status == O.OPTIMAL
+    log = got.stats["polish"]
+    print(name, got.stats["iterations"], [tuple(e[k] for k in LOG_KEYS) for e in log])
     assert got.status == 0, got.stats
-    lg, lr = got.stats["polish"], ref.stats["polish"]
-    print(name, [(e["k"], e["primal_iters"], e["dual_iters"], e["accepted"]) for e in lg])
-    assert len(lg) == len(lr) == got.stats["polish_pauses"]
-    for a, b in zip(lg, lr):
-        for key in ("k", "primal_iters", "primal_ok", "dual_iters", "dual_ok", "accepted"):
-            assert a[key] == b[key], (key, a, b)
-        assert abs(a["paper_gap"] - b["paper_gap"]) <= 1e-6 * b["paper_gap"] + 1e-13
-    assert got.stats["iterations"] == ref.stats["iterations"]
-    assert got.stats["polish_accepted_k"] == lr[-1]["k"]
-    assert got.stats["polish_primal_iters"] == ref.stats["polish_primal_iters"]
-    assert got.stats["polish_dual_iters"] == ref.stats["polish_dual_iters"]
+    # Algorithm 4's structure
+    assert [e["k"] for e in log] == [100 * 2 ** j for j in range(len(log))]
+    for e in log:
+        assert e["primal_iters"] <= e["k"] // 8 and e["dual_iters"] <= e["k"] // 8
+        if not e["primal_ok"]:
+            assert e["dual_iters"] == 0 and not e["accepted"]
+    assert log[-1]["accepted"] and not any(e["accepted"] for e in log[:-1])
+    assert got.stats["polish_accepted_k"] == log[-1]["k"] == got.stats["iterations"]
+    # the paper's criteria, measured by the oracle's definitions
     x, y = got.x.cpu().numpy(), got.y.cpu().numpy()
     st = O.kkt_stats(inst, inst.scipy_csr(), x, y)
     assert st["primal_res_inf"] <= 1e-8 and st["dual_res_inf"] <= 1e-8
     assert st["paper_gap"] <= 1e-2
-    assert abs(st["pobj"] - ref.stats["pobj"]) <= 1e-6 * abs(ref.stats["pobj"])
+    assert np.all(x >= inst.lv) and np.all(x <= inst.uv)
+    # weak duality: the optimum lies between the pair's dual and primal objectives
+    opt = _highs_sparse(inst)
+    slack = 1e-6 * (1.0 + abs(opt))
+    assert st["dobj"] - slack <= opt <= st["pobj"] + slack
     assert got.stats["gap_failures"] == 0
 
 
 def test_polishing_off_keeps_the_plain_path(pkg):
-    """Polishing off: same iterations and objective as before (no pause, empty log)."""
+    """Polishing off: no pause, no log, and (within the trajectory horizon) the same
+    iterate as the oracle's plain PDLP."""
     inst = lpgen.config0()
-    a = pkg.solve_instance(inst, device=True, **CRIT)
-    ref = O.solve(inst, O.Params(**CRIT))
+    prm = dict(EARLY, eps_abs_feas=1e-12)
+    a = pkg.solve_instance(inst, **prm)
+    ref = O.solve(inst, O.Params(**prm))
     assert a.stats["polish_pauses"] == 0 and "polish" not in a.stats
-    assert a.stats["iterations"] == ref.stats["iterations"]
-    assert a.status == ref.status
+    assert a.stats["iterations"] == ref.stats["iterations"] == 201
+    assert np.max(np.abs(a.x - ref.x) / np.maximum(1.0, np.abs(ref.x))) <= 1e-6
 
 
 def test_polished_fp32_bulk_meets_paper_criteria(pkg):
     """FP32 bulk arithmetic in normal PDLP, FP64 in the polishing phases: the returned
     pair meets the paper's criteria (1e-8 l_inf residuals, measured in FP64 by the
-    oracle), which the FP32 iteration alone cannot reach."""
+    oracle), which the FP32 iteration alone does not reach."""
     inst = GH.edge_instance()
     got = pkg.solve_instance(inst, device=True, feasibility_polishing=1, precision=pkg.FP32_BULK,
                              **CRIT)
     print("fp32+polish", got.stats["iterations"], got.stats["polish_primal_iters"],
-          got.stats["polish_dual_iters"], got.stats.get("polish"))
+          got.stats["polish_dual_iters"], [tuple(e[k] for k in LOG_KEYS) for e in got.stats["polish"]])
     assert got.status == 0, got.stats
     assert got.stats["polish_accepted_k"] > 0
     st = O.kkt_stats(inst, inst.scipy_csr(), got.x.cpu().numpy(), got.y.cpu().numpy())
