@@ -115,6 +115,7 @@ struct SpmvArgs {
   int grid_primal;
   double* part_dual;
   unsigned int* counter;
+  StepTable tab;
 };
 
 // Per-launch scalars and pointers every CTA reads once (kept in registers).
@@ -190,12 +191,23 @@ __device__ __forceinline__ void row_epilogue(const EpiCtx<T>& e, const EpiIn<T>&
 
 constexpr int kSpmvWarps = 4;
 constexpr int kSpmvThreads = 32 * kSpmvWarps;
-constexpr int kBatch = 8;
+#ifndef PDLP_SPMV_BATCH
+#define PDLP_SPMV_BATCH 8
+#endif
+constexpr int kBatch = PDLP_SPMV_BATCH;
+constexpr int kGrab = 2;  // items taken per visit of the dynamic work queue
 
-// Persistent kernel: warp w of the grid takes work items w, w + W, ... (W warps in
-// total).  Items [0, nchunks) are chunks of the long rows, the rest are SELL slices.
+// Persistent kernel over work items: items [0, nchunks) are chunks of the long rows,
+// the rest are SELL slices, in decreasing order of size.  kEpiDual assigns items
+// statically (warp w of W takes w, w + W, ...) because its step-size sums are
+// accumulated per warp and must not depend on timing; the other epilogues write
+// per-row results only and take items from a work queue (largest first), which
+// balances the power-law mix of item sizes.
+#ifndef PDLP_SPMV_MINB
+#define PDLP_SPMV_MINB 1
+#endif
 template <class T, int EPI>
-__global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs<T> a) {
+__global__ void __launch_bounds__(kSpmvThreads, PDLP_SPMV_MINB) k_spmv(SpmvArgs<T> a) {
   __shared__ double red[2 * kSpmvWarps];
   using A = typename AccT<T>::type;
 
@@ -250,7 +262,22 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs<T> a) {
   A c0 = (A)0, c1 = (A)0;
   const int64_t items = M.nchunks + M.nslices;
   const int64_t W = (int64_t)gridDim.x * kSpmvWarps;
-  for (int64_t it = (int64_t)blockIdx.x * kSpmvWarps + wib; it < items; it += W) {
+  constexpr bool kDynamic = EPI != kEpiDual;
+  int64_t it = kDynamic ? 0 : (int64_t)blockIdx.x * kSpmvWarps + wib;
+  int64_t grab_end = 0;
+  for (;;) {
+    if (kDynamic) {
+      if (it >= grab_end) {
+        unsigned int base = 0;
+        if (lane == 0) base = atomicAdd(&M.sched[0], (unsigned int)kGrab);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        it = base;
+        grab_end = (int64_t)base + kGrab;
+      }
+      if (it >= items) break;
+    } else if (it >= items) {
+      break;
+    }
     if (it >= M.nchunks) {
       // one SELL slice: 32 rows, one per lane, entries k-major
       const int64_t sl = it - M.nchunks;
@@ -320,9 +347,24 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs<T> a) {
         }
       }
     }
+    it += kDynamic ? 1 : W;
   }
 
-  if (EPI != kEpiDual) return;
+  if (kDynamic) {
+    // the last CTA out resets the queue for the next launch on the stream (every
+    // warp's last visit precedes its CTA's arrival)
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned prev = atomicAdd(&M.sched[1], 1u);
+      if (prev == gridDim.x - 1) {
+        M.sched[0] = 0u;
+        M.sched[1] = 0u;
+        __threadfence();
+      }
+    }
+    return;
+  }
 
   // step-size sums: per CTA, then the last CTA reduces in fixed order and decides
   double v[2] = {(double)c0, (double)c1};
@@ -333,27 +375,51 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs<T> a) {
     a.part_dual[G + blockIdx.x] = v[1];
   }
   if (!last_block_arrival(a.counter)) return;
-  const double dx2 = block_sum_array<kSpmvWarps>(a.part_primal, a.grid_primal, red);
-  const double dy2_t = block_sum_array<kSpmvWarps>(a.part_dual, G, red);
-  const double in_t = block_sum_array<kSpmvWarps>(a.part_dual + G, G, red);
-  double lc0[2] = {0.0, 0.0};
-  for (int i = threadIdx.x; i < M.R0; i += blockDim.x) {
-    lc0[0] += ((volatile double*)M.long_contrib)[2 * i];
-    lc0[1] += ((volatile double*)M.long_contrib)[2 * i + 1];
+  // the per-CTA partials of both kernels and the long rows' contributions, read from
+  // L2 four strides at a time (one latency per four loads), fixed-order sums
+  double t5[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // dx2, dy2, inter, long dy2, long inter
+  {
+    const int64_t n0 = a.grid_primal, n1 = G, n2 = M.R0;
+    const int64_t nmax = max(n0, max(n1, n2));
+    const int64_t B = blockDim.x;
+    for (int64_t i0 = threadIdx.x; i0 < nmax; i0 += 4 * B) {
+      double q[5][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t i = i0 + u * B;
+        q[0][u] = i < n0 ? __ldcg(a.part_primal + i) : 0.0;
+        q[1][u] = i < n1 ? __ldcg(a.part_dual + i) : 0.0;
+        q[2][u] = i < n1 ? __ldcg(a.part_dual + G + i) : 0.0;
+        q[3][u] = i < n2 ? __ldcg(M.long_contrib + 2 * i) : 0.0;
+        q[4][u] = i < n2 ? __ldcg(M.long_contrib + 2 * i + 1) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) t5[j] += q[j][u];
+    }
   }
-  block_sum<2, kSpmvWarps>(lc0, red);
+  __shared__ double red5[5 * kSpmvWarps];
+  block_sum<5, kSpmvWarps>(t5, red5);
   if (threadIdx.x != 0) return;
-  const double dy2 = dy2_t + lc0[0];
-  const double inter = in_t + lc0[1];
+  const double dx2 = t5[0];
+  const double dy2 = t5[1] + t5[3];
+  const double inter = t5[2] + t5[4];
   DevState* s = a.st;
   const double omega = s->omega, eta = s->eta;
   // Algorithm 2 with the interaction taken in magnitude (Eq. (5) for K = -A)
   const double num = omega * dx2 + dy2 / omega;
   const double den = 2.0 * fabs(inter);
   const double eta_bar = den > 0.0 ? num / den : INFINITY;
-  const double kf = (double)(s->k + 2);
-  const double red_f = 1.0 - pow(kf, -0.3);
-  const double grow_f = 1.0 + pow(kf, -0.6);
+  double red_f, grow_f;
+  if (s->k < a.tab.len) {
+    red_f = a.tab.f[2 * s->k];
+    grow_f = a.tab.f[2 * s->k + 1];
+  } else {
+    const double kf = (double)(s->k + 2);
+    red_f = 1.0 - pow(kf, -0.3);
+    grow_f = 1.0 + pow(kf, -0.6);
+  }
   const double eta_new = fmin(red_f * eta_bar, grow_f * eta);
   s->attempts += 1;
   s->last_dx2 = dx2;
@@ -380,6 +446,21 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs<T> a) {
     s->rejected += 1;
     if (s->retries >= s->max_retries) s->error = 2;
   }
+}
+
+__global__ void k_step_table(double* f, int64_t len) {
+  for (int64_t k = gtid2(); k < len; k += gstride2()) {
+    const double kf = (double)(k + 2);
+    f[2 * k] = 1.0 - pow(kf, -0.3);
+    f[2 * k + 1] = 1.0 + pow(kf, -0.6);
+  }
+}
+
+void fill_step_table(double* f, int64_t len, cudaStream_t s) {
+  const int64_t need = (len + 255) / 256;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 8));
+  k_step_table<<<grid, 256, 0, s>>>(f, len);
+  PDLP_LAUNCH_CHECK();
 }
 
 // ---------------------------------------------------------------------------
@@ -419,8 +500,9 @@ void launch_primal(const IterBuffers<T>& b, DevState* st, double* part, int grid
 template <class T>
 void launch_spmv_dual(const Mat<T>& A, const IterBuffers<T>& b, DevState* st,
                       const double* part_primal, int grid_primal, double* part_dual,
-                      unsigned int* counter, int grid, cudaStream_t s) {
+                      unsigned int* counter, StepTable tab, int grid, cudaStream_t s) {
   SpmvArgs<T> a{};
+  a.tab = tab;
   a.M = A;
   a.b = b;
   a.st = st;
@@ -457,8 +539,8 @@ void launch_spmv_plain(const Mat<T>& M, const T* src, T* dst, int grid, cudaStre
   template int spmv_grid<T>(const Mat<T>&, int);                                            \
   template void launch_primal<T>(const IterBuffers<T>&, DevState*, double*, int, cudaStream_t); \
   template void launch_spmv_dual<T>(const Mat<T>&, const IterBuffers<T>&, DevState*,        \
-                                    const double*, int, double*, unsigned int*, int,        \
-                                    cudaStream_t);                                          \
+                                    const double*, int, double*, unsigned int*, StepTable,  \
+                                    int, cudaStream_t);                                     \
   template void launch_spmv_avg<T>(const Mat<T>&, const IterBuffers<T>&, DevState*, int,    \
                                    cudaStream_t);                                           \
   template void launch_spmv_plain<T>(const Mat<T>&, const T*, T*, int, cudaStream_t);

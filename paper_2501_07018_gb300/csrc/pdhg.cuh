@@ -28,6 +28,15 @@ struct IterBuffers {
 
 enum SpmvEpilogue { kEpiPlain = 0, kEpiDual = 1, kEpiAverage = 2 };
 
+// Algorithm 2's factors 1 - (k+2)^-0.3 and 1 + (k+2)^-0.6 for accepted counts k in
+// [0, len): f[2k], f[2k+1].  Precomputed (same device pow) so that the accept
+// decision at the end of the A-side SpMV does not evaluate pow on a single lane.
+struct StepTable {
+  const double* f;
+  int64_t len;
+};
+void fill_step_table(double* f, int64_t len, cudaStream_t s);
+
 template <class T>
 int spmv_grid(const Mat<T>& M, int epi);
 int primal_grid(int64_t n);
@@ -43,7 +52,7 @@ void launch_primal(const IterBuffers<T>& b, DevState* st, double* part, int grid
 template <class T>
 void launch_spmv_dual(const Mat<T>& A, const IterBuffers<T>& b, DevState* st,
                       const double* part_primal, int grid_primal, double* part_dual,
-                      unsigned int* counter, int grid, cudaStream_t s);
+                      unsigned int* counter, StepTable tab, int grid, cudaStream_t s);
 
 // A'y' with the running-average update (Algorithm 1) fused; a no-op when the last
 // attempt was rejected.

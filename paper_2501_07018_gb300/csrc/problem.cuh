@@ -33,6 +33,8 @@ struct Mat {
   unsigned int* long_cnt = nullptr;  // [R0] arrival counters (kept at 0 between launches)
   double* long_part = nullptr;       // [nchunks] chunk partial sums
   double* long_contrib = nullptr;    // [R0 * 2] per-long-row reduction contributions
+  unsigned int* sched = nullptr;     // [2] dynamic work queue: next item, CTAs done
+                                     // (both back at 0 between launches)
   // SELL-32 of rows [R0, rows)
   int64_t nslices = 0;
   int64_t* slice_ptr = nullptr;  // [nslices+1]

@@ -670,6 +670,8 @@ void build_sell(DeviceArena& arena, Mat<T>& M, const double* val64, cudaStream_t
   M.long_contrib = arena.alloc<double>(2 * R0);
   PDLP_CUDA_CHECK(cudaMemsetAsync(M.long_cnt, 0, sizeof(unsigned int) * std::max<int64_t>(1, R0), s));
   PDLP_CUDA_CHECK(cudaMemsetAsync(M.long_contrib, 0, sizeof(double) * 2 * std::max<int64_t>(1, R0), s));
+  M.sched = arena.alloc<unsigned int>(2);
+  PDLP_CUDA_CHECK(cudaMemsetAsync(M.sched, 0, 2 * sizeof(unsigned int), s));
 
   // SELL-32 of the remaining rows
   M.nslices = (rows - R0 + 31) / 32;

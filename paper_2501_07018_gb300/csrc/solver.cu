@@ -559,6 +559,8 @@ struct Solver {
   GapScratch gsc{};
   double* dist_part = nullptr;
   double* dist_out = nullptr;
+  double* step_tab = nullptr;  // Algorithm 2's factors by accepted count (StepTable)
+  int64_t step_len = 0;
   EventTimer timer;
   GapStats gap_stats;
   int64_t launches = 0;
@@ -698,13 +700,25 @@ struct Solver {
     return kkt_finish(h, P.c_norm, P.b_norm);
   }
 
+  // the step-factor table covers accepted counts [0, upto]; it grows by doubling
+  void ensure_step_table(int64_t upto) {
+    if (upto < step_len) return;
+    int64_t len = std::max<int64_t>(4096, 2 * step_len);
+    while (len <= upto) len *= 2;
+    step_tab = arena.alloc<double>(2 * len);
+    fill_step_table(step_tab, len, s);
+    launches++;
+    step_len = len;
+  }
+
   // one step attempt = three launches (see file comment)
   void launch_slot(Run<T>& r) {
     int e0 = timer.begin(s);
     launch_primal<T>(r.b, r.dst, part_primal, g_primal, s);
     timer.end(e0, 2, s);
     int e1 = timer.begin(s);
-    launch_spmv_dual<T>(P.A, r.b, r.dst, part_primal, g_primal, part_dual, counters, g_a, s);
+    launch_spmv_dual<T>(P.A, r.b, r.dst, part_primal, g_primal, part_dual, counters,
+                        StepTable{step_tab, step_len}, g_a, s);
     timer.end(e1, 0, s);
     int e2 = timer.begin(s);
     launch_spmv_avg<T>(P.AT, r.b, r.dst, g_at, s);
@@ -799,6 +813,7 @@ struct Solver {
       const int64_t j_art = steps_to_artificial(r.k, r.t);
       if (r.k + j_art < target) target = r.k + j_art;
       // launch attempts until `target` accepted iterations (rejections need more)
+      ensure_step_table(target);
       bool error = false;
       while (r.k < target) {
         const int64_t need = (trace_iters > r.k) ? 1 : (target - r.k);
