@@ -194,8 +194,27 @@ constexpr int kSpmvThreads = 32 * kSpmvWarps;
 #ifndef PDLP_SPMV_BATCH
 #define PDLP_SPMV_BATCH 8
 #endif
-constexpr int kBatch = PDLP_SPMV_BATCH;
-constexpr int kGrab = 2;  // items taken per visit of the dynamic work queue
+#ifndef PDLP_SPMV_FBATCH
+#define PDLP_SPMV_FBATCH 8
+#endif
+// entries per lane whose loads and gathers are in flight together
+template <class T>
+__host__ __device__ constexpr int batch_of() {
+  return sizeof(T) == 8 ? PDLP_SPMV_BATCH : PDLP_SPMV_FBATCH;
+}
+#ifndef PDLP_SPMV_GRAB
+#define PDLP_SPMV_GRAB 2
+#endif
+#ifndef PDLP_SPMV_DYNAMIC
+#define PDLP_SPMV_DYNAMIC 1
+#endif
+constexpr int kGrab = PDLP_SPMV_GRAB;  // items taken per visit of the dynamic work queue
+
+// CTAs per SM the register budget must allow (8 = 32 warps): the gathers need the
+// warps in flight to cover their latency
+#ifndef PDLP_SPMV_MINB
+#define PDLP_SPMV_MINB(T) 8
+#endif
 
 // Persistent kernel over work items: items [0, nchunks) are chunks of the long rows,
 // the rest are SELL slices, in decreasing order of size.  kEpiDual assigns items
@@ -203,11 +222,8 @@ constexpr int kGrab = 2;  // items taken per visit of the dynamic work queue
 // accumulated per warp and must not depend on timing; the other epilogues write
 // per-row results only and take items from a work queue (largest first), which
 // balances the power-law mix of item sizes.
-#ifndef PDLP_SPMV_MINB
-#define PDLP_SPMV_MINB 1
-#endif
 template <class T, int EPI>
-__global__ void __launch_bounds__(kSpmvThreads, PDLP_SPMV_MINB) k_spmv(SpmvArgs<T> a) {
+__global__ void __launch_bounds__(kSpmvThreads, PDLP_SPMV_MINB(T)) k_spmv(SpmvArgs<T> a) {
   __shared__ double red[2 * kSpmvWarps];
   using A = typename AccT<T>::type;
 
@@ -262,7 +278,7 @@ __global__ void __launch_bounds__(kSpmvThreads, PDLP_SPMV_MINB) k_spmv(SpmvArgs<
   A c0 = (A)0, c1 = (A)0;
   const int64_t items = M.nchunks + M.nslices;
   const int64_t W = (int64_t)gridDim.x * kSpmvWarps;
-  constexpr bool kDynamic = EPI != kEpiDual;
+  constexpr bool kDynamic = PDLP_SPMV_DYNAMIC && EPI != kEpiDual;
   int64_t it = kDynamic ? 0 : (int64_t)blockIdx.x * kSpmvWarps + wib;
   int64_t grab_end = 0;
   for (;;) {
@@ -290,6 +306,7 @@ __global__ void __launch_bounds__(kSpmvThreads, PDLP_SPMV_MINB) k_spmv(SpmvArgs<
       const T* __restrict__ vp = M.sell_val + M.slice_ptr[sl] + lane;
       // two independent FMA chains (even / odd entries) for instruction-level parallelism
       T acc_e = (T)0, acc_o = (T)0;
+      constexpr int kBatch = batch_of<T>();
       for (int k0 = 0; k0 < L; k0 += kBatch) {
         int cr[kBatch];
         T vr[kBatch], xr[kBatch];
@@ -328,22 +345,34 @@ __global__ void __launch_bounds__(kSpmvThreads, PDLP_SPMV_MINB) k_spmv(SpmvArgs<
 #pragma unroll 4
       for (int64_t p = pb + lane; p < pe; p += 32) acc = fma(valp[p], src[colp[p]], acc);
       const double part = warp_sum((double)acc);
-      if (lane == 0) {
-        M.long_part[ci] = part;
-        __threadfence();
-        const unsigned prev = atomicAdd(&M.long_cnt[row], 1u);
-        if (prev == (unsigned)(nch - 1)) {
+      // a row of one chunk is finished here; otherwise the last of its chunks to
+      // arrive adds the chunk sums (lane q holds chunk q; fixed tree over lanes)
+      bool finish = nch == 1;
+      double sum = part;
+      if (!finish) {
+        unsigned prev = 0;
+        if (lane == 0) {
+          M.long_part[ci] = part;
           __threadfence();
-          double sum = 0.0;
-          for (int64_t q = 0; q < nch; ++q) sum += ((volatile double*)M.long_part)[first + q];
-          M.long_cnt[row] = 0u;
-          A d0 = (A)0, d1 = (A)0;
-          const EpiIn<T> ein = load_epi<T, EPI>(e, row);
-          row_epilogue<T, EPI, A>(e, ein, row, (T)sum, d0, d1);
-          if (EPI == kEpiDual) {
-            M.long_contrib[2 * row] = (double)d0;
-            M.long_contrib[2 * row + 1] = (double)d1;
-          }
+          prev = atomicAdd(&M.long_cnt[row], 1u);
+        }
+        prev = __shfl_sync(0xffffffffu, prev, 0);
+        finish = prev == (unsigned)(nch - 1);
+        if (finish) {
+          __threadfence();
+          double v = 0.0;
+          for (int64_t q = lane; q < nch; q += 32) v += __ldcg(M.long_part + first + q);
+          sum = warp_sum(v);
+          if (lane == 0) M.long_cnt[row] = 0u;
+        }
+      }
+      if (finish && lane == 0) {
+        A d0 = (A)0, d1 = (A)0;
+        const EpiIn<T> ein = load_epi<T, EPI>(e, row);
+        row_epilogue<T, EPI, A>(e, ein, row, (T)sum, d0, d1);
+        if (EPI == kEpiDual) {
+          M.long_contrib[2 * row] = (double)d0;
+          M.long_contrib[2 * row + 1] = (double)d1;
         }
       }
     }
@@ -365,6 +394,7 @@ __global__ void __launch_bounds__(kSpmvThreads, PDLP_SPMV_MINB) k_spmv(SpmvArgs<
     }
     return;
   }
+  if (EPI != kEpiDual) return;  // only the A-side product feeds Algorithm 2
 
   // step-size sums: per CTA, then the last CTA reduces in fixed order and decides
   double v[2] = {(double)c0, (double)c1};

@@ -11,13 +11,17 @@ namespace pdlp {
 // Storage of a (row- and column-renumbered) sparse matrix for the fused SpMV kernels.
 //   Rows are numbered by decreasing length.  The first R0 rows (every row longer than
 //   kLongRow, rounded up to a multiple of 32) stay in CSR and are processed in chunks
-//   of kChunk entries, one warp per chunk; chunk partial sums of a row are combined
-//   in chunk order by the last chunk to finish.  The remaining rows are stored as
-//   SELL-32: slice s holds rows R0 + 32 s ... R0 + 32 s + 31, padded to the length of
-//   its first (longest) row, entry k of lane l at slice_ptr[s] + 32 k + l; padding
-//   entries have value 0.  One warp processes one slice, one row per lane.
+//   of kChunk entries, one warp per chunk; a row of several chunks is finished by the
+//   last of its chunks to arrive, which adds the chunk sums in a fixed order.  The
+//   remaining rows are stored as SELL-32: slice s holds rows R0 + 32 s ...
+//   R0 + 32 s + 31, padded to the length of its first (longest) row, entry k of lane l
+//   at slice_ptr[s] + 32 k + l; padding entries have value 0.  One warp processes one
+//   slice, one row per lane.
+#ifndef PDLP_CHUNK
+#define PDLP_CHUNK 4096
+#endif
 constexpr int kLongRow = 256;
-constexpr int kChunk = 512;
+constexpr int kChunk = PDLP_CHUNK;
 
 template <class T>
 struct Mat {

@@ -47,13 +47,18 @@ def _trace_parity(pkg, inst, iters=100, **prm):
     return res, ora, errs
 
 
-@pytest.mark.parametrize("name", ["config0", "edge", "powerlaw"])
+@pytest.mark.parametrize("name", ["config0", "edge", "edge_long", "powerlaw"])
 def test_trace_parity_first_100_iterations(pkg, name):
-    """Iterates, accepted steps and restart decisions of the first 100 iterations."""
+    """Iterates, accepted steps and restart decisions of the first 100 iterations.
+    ``edge_long`` has a row of A and a row of A' that span several chunks of the
+    long-row path (chunk sums combined by the last chunk to finish)."""
     if name == "config0":
         inst = lpgen.config0()
     elif name == "edge":
         inst = GH.edge_instance()
+    elif name == "edge_long":
+        inst = GH.edge_instance(seed=12, m=12000, n=24000, dense_row_nnz=20000,
+                                dense_col_nnz=10000)
     else:
         inst = lpgen.config1(scale=0.002)
     res, ora, errs = _trace_parity(pkg, inst)
