@@ -47,6 +47,9 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--iters-per-step", type=int, default=5000)
+    ap.add_argument("--warmup-iters-per-step", type=int, default=None,
+                    help="iterations of each warm-up solve (default: --iters-per-step); "
+                         "shorter warm-ups keep a profiler's launch list small")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the LP (testing only)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
                     help="arithmetic of the PDHG loop (fp32 = FP32 bulk, FP64 checks)")
@@ -229,6 +232,25 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def copy_bandwidth_gbs(torch, stream):
+    """Device-to-device copy of 2 GiB on this GPU (read + write bytes / CUDA-event
+    time, best of 5): context for the roofline, whose peak is the pool's measured one."""
+    a = torch.empty(1 << 28, dtype=torch.float64, device="cuda")
+    b = torch.empty_like(a)
+    a.fill_(1.0)
+    best = 0.0
+    for _ in range(6):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.copy_(a)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = max(best, 2 * a.numel() * 8 / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    del a, b
+    return best
+
+
+
 def aggregate_over_ranks(dist, secs, iters, launches, device):
     """Whole-job figures of independent replicas: the slowest rank's seconds and the
     iterations and kernel launches of all ranks (one all_reduce each; works on any
@@ -269,16 +291,17 @@ def run_ours(args):
 
     prec = pkg.FP64 if args.precision == "fp64" else pkg.FP32_BULK
 
-    def step(profile=1):
-        return pkg.solve(inst.m, inst.n, *d, max_iters=iters, eps_rel_kkt=0.0, profile=profile,
+    def step(profile=1, n_iters=iters):
+        return pkg.solve(inst.m, inst.n, *d, max_iters=n_iters, eps_rel_kkt=0.0, profile=profile,
                          precision=prec)
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
+    warmup_launches = 0
     for _ in range(max(args.warmup, 3)):
-        step()
+        warmup_launches += step(n_iters=args.warmup_iters_per_step or iters).stats["kernel_launches"]
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
@@ -300,6 +323,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks = clk.stop()
     secs = e0.elapsed_time(e1) / 1e3
+    box_copy = copy_bandwidth_gbs(torch, stream)
     secs_max, total_iters, total_launches = aggregate_over_ranks(
         dist, secs, agg["iterations"], agg["kernel_launches"], "cuda")
     value = total_iters / secs_max
@@ -324,7 +348,8 @@ def run_ours(args):
                 "traffic": traffic_from_profiles(f"{key}_{args.precision}", bytes_per),
                 "kernel": desc, "algorithmic_bytes_per_launch": bytes_per,
                 "ms_per_launch": per_launch_s * 1e3,
-                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"}
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
+                "copy_gbs_this_gpu": box_copy}
     other = {c[0]: {"ms_per_launch": c[1] / c[2], "gbs": c[3] / (c[1] / c[2] / 1e3) / 1e9,
                     "algorithmic_bytes_per_launch": c[3], "launches": c[2],
                     "share_of_step": c[1] / (1e3 * secs)} for c in cand}
@@ -339,7 +364,7 @@ def run_ours(args):
                       "l2": "no flush: the matrix (A and A' ~1.2 GB FP64) is far larger than L2",
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
            "roofline": roofline, "kernels": other, "clocks": clocks,
-           "gpu_launches": int(total_launches)}
+           "gpu_launches": int(total_launches), "warmup_gpu_launches": int(warmup_launches)}
 
     # e2e: host pinned buffers, copies inside the timed region
     pinned = []

@@ -61,6 +61,15 @@ used):
       of the termination criteria in force, tested on the restart candidate at the
       checks and at the phase's last iteration; the primal phase's output is its
       returned candidate, the dual phase's likewise even when it hits its budget.
+  R22 Infeasibility detection (Sec. 3, App. C) runs at every check of normal PDLP,
+      after the termination test, on three candidate directions in this order: the
+      difference of the last two iterates, the current iterate, the average since the
+      last restart (positive scalings of the paper's "normalized" sequences; the tests
+      are scale invariant).  Each candidate's y is projected onto Y and paired with
+      r = proj_R(-A'y), its x onto the recession cone of the box and paired with
+      s = proj_Sbar(-Ax); the tests run on the unscaled LP.  The returned point is
+      (current x, certificate y) for primal infeasibility and (certificate x, current
+      y) for dual infeasibility.
 """
 from __future__ import annotations
 
@@ -104,6 +113,8 @@ class Params:
     fixed_omega: float | None = None
     restarts: bool = True
     feasibility_polishing: bool = False  # Algorithm 4 (Sec. 5)
+    detect_infeasibility: bool = True  # Sec. 3 "Infeasibility detection", App. C
+    eps_infeas: float = 1e-9
 
 
 # ----------------------------------------------------------------------------
@@ -155,6 +166,41 @@ def proj_R(g, lv, uv):
     r = np.where(~lf & uf, np.minimum(g, 0.0), r)
     r = np.where(~lf & ~uf, 0.0, r)
     return r
+
+
+def proj_Y(y, lc, uc):
+    """Projection onto the dual sign set Y (Sec. 2): R^+ for a row with only a finite
+    lower bound, R^- with only a finite upper bound, {0} for a free row, R otherwise."""
+    lf, uf = np.isfinite(lc), np.isfinite(uc)
+    out = y.copy()
+    out = np.where(lf & ~uf, np.maximum(y, 0.0), out)
+    out = np.where(~lf & uf, np.minimum(y, 0.0), out)
+    out = np.where(~lf & ~uf, 0.0, out)
+    return out
+
+
+def proj_Xbar(x, lv, uv):
+    """Projection onto the recession cone of the variable box (App. C): {0} for a
+    variable with two finite bounds, R^+ with only a finite lower bound, R^- with only a
+    finite upper bound, R for a free variable."""
+    lf, uf = np.isfinite(lv), np.isfinite(uv)
+    out = x.copy()
+    out = np.where(lf & uf, 0.0, out)
+    out = np.where(lf & ~uf, np.maximum(x, 0.0), out)
+    out = np.where(~lf & uf, np.minimum(x, 0.0), out)
+    return out
+
+
+def proj_Sbar(s, lc, uc):
+    """Projection onto the slack cone S-bar of App. C: {0} for a row with two finite
+    bounds, R^+ with only a finite upper bound, R^- with only a finite lower bound, R
+    for a free row."""
+    lf, uf = np.isfinite(lc), np.isfinite(uc)
+    out = s.copy()
+    out = np.where(lf & uf, 0.0, out)
+    out = np.where(~lf & uf, np.maximum(s, 0.0), out)
+    out = np.where(lf & ~uf, np.minimum(s, 0.0), out)
+    return out
 
 
 # ----------------------------------------------------------------------------
@@ -464,6 +510,51 @@ def kkt_stats(inst, A_orig, x, y):
     )
 
 
+# ----------------------------------------------------------------------------
+# infeasibility certificates (Sec. 3 "Infeasibility detection", App. C)
+# ----------------------------------------------------------------------------
+
+def primal_infeasibility_measures(inst, A_orig, y):
+    """For a direction y (unscaled LP): y-bar = proj_Y(y), the reduced costs that make
+    ||A'y-bar + r||_inf smallest over R, r = proj_R(-A'y-bar), and the two numbers of
+    App. C's test: the dual objective lc'y+ - uc'y- + lv'r+ - uv'r- of (y-bar, r) and
+    ||A'y-bar + r||_inf.  Returns (y_bar, objective, residual)."""
+    yb = proj_Y(y, inst.lc, inst.uc)
+    q = A_orig.T @ yb
+    r = proj_R(-q, inst.lv, inst.uv)
+    obj = -p_fn(-yb, inst.lc, inst.uc) - p_fn(-r, inst.lv, inst.uv)
+    res = float(np.max(np.abs(q + r))) if q.size else 0.0
+    return yb, obj, res
+
+
+def dual_infeasibility_measures(inst, A_orig, x):
+    """For a direction x (unscaled LP): x-bar = proj_Xbar(x), s = proj_Sbar(-A x-bar)
+    (the slack that makes ||A x-bar + s||_inf smallest), and App. C's numbers c'x-bar and
+    ||A x-bar + s||_inf.  Returns (x_bar, c'x_bar, residual)."""
+    xb = proj_Xbar(x, inst.lv, inst.uv)
+    p = A_orig @ xb
+    sl = proj_Sbar(-p, inst.lc, inst.uc)
+    res = float(np.max(np.abs(p + sl))) if p.size else 0.0
+    return xb, float(np.dot(inst.c, xb)), res
+
+
+def infeasibility_certificate(inst, A_orig, candidates, eps):
+    """App. C's tests on the candidate directions (unscaled (x, y) pairs, in order):
+    primal infeasibility -- objective > 0 and residual <= eps * objective -- on each
+    candidate's y, then dual infeasibility -- c'x-bar < 0 and residual <= eps |c'x-bar| --
+    on each candidate's x.  Returns (PRIMAL_INFEASIBLE, y_bar), (DUAL_INFEASIBLE, x_bar)
+    or None."""
+    for _, y in candidates:
+        yb, obj, res = primal_infeasibility_measures(inst, A_orig, y)
+        if obj > 0.0 and res <= eps * obj:
+            return PRIMAL_INFEASIBLE, yb
+    for x, _ in candidates:
+        xb, cx, res = dual_infeasibility_measures(inst, A_orig, x)
+        if cx < 0.0 and res <= eps * abs(cx):
+            return DUAL_INFEASIBLE, xb
+    return None
+
+
 def converged(st, prm: Params):
     if prm.termination_mode == 0:
         return st["rel_kkt"] <= prm.eps_rel_kkt
@@ -496,12 +587,15 @@ class PdlpRun:
     iteration's checks and restart done), returning None; the state stays in the
     object, so a paused run continues where it stopped."""
 
-    def __init__(self, lp, prm: Params, x, y, omega, eta_hat, goal, max_iters, trace_iters=0):
+    def __init__(self, lp, prm: Params, x, y, omega, eta_hat, goal, max_iters, trace_iters=0,
+                 infeas=None):
         m, n = lp.A.shape
         self.lp, self.prm, self.goal, self.max_iters = lp, prm, goal, max_iters
+        self.infeas = infeas  # infeas(candidates) -> (status, x, y) or None (scaled)
         self.m, self.n = m, n
         self.x, self.y = np.array(x, dtype=float), np.array(y, dtype=float)
         self.Ax, self.ATy = lp.A @ self.x, lp.AT @ self.y
+        self.x_prev, self.y_prev = self.x.copy(), self.y.copy()  # z before the last step
         self.omega, self.eta_hat = omega, eta_hat
         self.k = self.t = 0
         self.x0, self.y0 = self.x.copy(), self.y.copy()  # z^{n,0}
@@ -558,6 +652,7 @@ class PdlpRun:
             self.SAx += eta * Axn
             self.SATy += eta * ATyn
             self.W += eta
+            self.x_prev, self.y_prev = x, y
             self.x, self.y, self.Ax, self.ATy = xn, yn, Axn, ATyn
             self.eta_hat = eta_new
             self.t += 1
@@ -591,6 +686,10 @@ class PdlpRun:
             if is_check or is_limit:  # R9
                 if self.goal(cand[0], cand[1]):
                     return OPTIMAL, cand[0], cand[1]
+                if self.infeas is not None:  # R22
+                    out = self.infeas([(xn - self.x_prev, yn - self.y_prev), (xn, yn), (xa, ya)])
+                    if out is not None:
+                        return out
                 if is_limit:
                     return ITERATION_LIMIT, cand[0], cand[1]
             kind = RESTART_NONE
@@ -645,8 +744,21 @@ def solve(inst, prm: Params | None = None, trace_iters: int = 0, lp: ScaledLP | 
     def measures(xs, ys):
         return kkt_stats(inst, lp.A_orig, lp.d2 * xs, lp.d1 * ys)
 
+    def infeas(cands):
+        """Certificate directions are tested on the unscaled LP; a certificate is
+        returned in the scaled space like every other result (R22)."""
+        out = infeasibility_certificate(
+            inst, lp.A_orig, [(lp.d2 * cx, lp.d1 * cy) for cx, cy in cands], prm.eps_infeas)
+        if out is None:
+            return None
+        status, v = out
+        xs, ys = cands[1]
+        if status == PRIMAL_INFEASIBLE:
+            return status, xs, v / lp.d1
+        return status, v / lp.d2, ys
+
     run = PdlpRun(lp, prm, x, y, omega, eta_hat, lambda xs, ys: converged(measures(xs, ys), prm),
-                  prm.max_iters, trace_iters)
+                  prm.max_iters, trace_iters, infeas if prm.detect_infeasibility else None)
     polish = None
     if prm.feasibility_polishing:
         status, xs, ys, polish = _solve_polished(lp, prm, run, measures)

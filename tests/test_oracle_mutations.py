@@ -108,3 +108,45 @@ def test_wrong_pause_schedule_is_caught(monkeypatch):
     monkeypatch.setattr(O, "polish_pauses", bad)
     with pytest.raises(AssertionError):
         PP.test_pause_schedule_and_phase_budgets()
+
+
+# --- infeasibility detection (Sec. 3, App. C) --------------------------------------
+from tests import test_oracle_infeasibility as PI  # noqa: E402
+
+
+def test_wrong_dual_cone_is_caught(monkeypatch):
+    # Y taken as R^+ for rows with only an upper bound (sign flipped)
+    def bad(y, lc, uc):
+        lf, uf = np.isfinite(lc), np.isfinite(uc)
+        out = y.copy()
+        out = np.where(lf & ~uf, np.maximum(y, 0.0), out)
+        out = np.where(~lf & uf, np.maximum(y, 0.0), out)
+        return np.where(~lf & ~uf, 0.0, out)
+    monkeypatch.setattr(O, "proj_Y", bad)
+    with pytest.raises(AssertionError):
+        PI.test_two_variable_closed_forms()
+
+
+def test_dropped_reduced_cost_term_is_caught(monkeypatch):
+    # objective of the certificate without the lv'r+ - uv'r- term
+    def bad(inst, A_orig, y):
+        yb = O.proj_Y(y, inst.lc, inst.uc)
+        q = A_orig.T @ yb
+        r = O.proj_R(-q, inst.lv, inst.uv)
+        return yb, -O.p_fn(-yb, inst.lc, inst.uc), float(np.max(np.abs(q + r)))
+    monkeypatch.setattr(O, "primal_infeasibility_measures", bad)
+    with pytest.raises(AssertionError):
+        PI.test_bound_driven_infeasibility_closed_form()
+
+
+def test_wrong_slack_cone_is_caught(monkeypatch):
+    # S-bar with the one-sided cases swapped
+    def bad(s, lc, uc):
+        lf, uf = np.isfinite(lc), np.isfinite(uc)
+        out = s.copy()
+        out = np.where(lf & uf, 0.0, out)
+        out = np.where(~lf & uf, np.minimum(s, 0.0), out)
+        return np.where(lf & ~uf, np.maximum(s, 0.0), out)
+    monkeypatch.setattr(O, "proj_Sbar", bad)
+    with pytest.raises(AssertionError):
+        PI.test_two_variable_closed_forms()
