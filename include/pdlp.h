@@ -40,8 +40,8 @@ extern "C" {
 #define PDLP_OPTIMAL 0            /* termination criterion met                    */
 #define PDLP_ITERATION_LIMIT 1    /* params->max_iters accepted iterations done   */
 #define PDLP_TIME_LIMIT 2         /* params->time_limit_s exceeded                */
-#define PDLP_PRIMAL_INFEASIBLE 3  /* reserved (infeasibility certificate, App. D) */
-#define PDLP_DUAL_INFEASIBLE 4    /* reserved (infeasibility certificate, App. D) */
+#define PDLP_PRIMAL_INFEASIBLE 3  /* App. C certificate found: y returns it        */
+#define PDLP_DUAL_INFEASIBLE 4    /* App. C certificate found: x returns the ray    */
 #define PDLP_NUMERICAL_ERROR 5    /* non-finite step or step-retry cap reached    */
 #define PDLP_INVALID_ARGUMENT (-1)
 #define PDLP_OUT_OF_MEMORY (-2)
@@ -104,6 +104,26 @@ typedef struct {
   int64_t polish_log_cap;  /* rows available in polish_log                          */
   double* polish_log;      /* host [polish_log_cap * PDLP_POLISH_LOG_COLS] or NULL:
                               one row per pause (see PDLP_POLISH_LOG_COLS)          */
+  int detect_infeasibility; /* 1 (default): at every check of normal PDLP, after the
+                              termination test, test three candidate directions --
+                              the difference of the last two iterates, the current
+                              iterate, the average since the last restart -- as
+                              certificates of App. C on the unscaled LP: y projected
+                              onto Y with r = proj_R(-A'y): primal infeasible if
+                              lc'y+ - uc'y- + lv'r+ - uv'r- > 0 and ||A'y + r||_inf
+                              <= eps_infeas times it (status 3, y = the certificate,
+                              x = current); x projected onto the recession cone of
+                              the box with s = proj_Sbar(-Ax): dual infeasible if
+                              c'x < 0 and ||Ax + s||_inf <= eps_infeas |c'x| (status
+                              4, x = the ray, not clipped to the bounds, y = current).
+                              Costs four sparse products per check.                */
+  double eps_infeas;       /* App. C's threshold: 1e-9                              */
+  int reduced_costs;       /* reduced costs r of the dual residual and objective in
+                              every optimality measure: 0 (default) r = proj_R(c -
+                              A'y) (Sec. 2); 1 App. A's choice, r_i = (c - A'y)_i
+                              when it is positive and x_i - lv_i <= |x_i|, or
+                              negative and uv_i - x_i <= |x_i|, else 0 (robust to
+                              huge bounds; changes the measures, not the iterates) */
 } pdlp_params;
 
 /* Row of params->polish_log for one pause of Algorithm 4:

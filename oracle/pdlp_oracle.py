@@ -115,6 +115,7 @@ class Params:
     feasibility_polishing: bool = False  # Algorithm 4 (Sec. 5)
     detect_infeasibility: bool = True  # Sec. 3 "Infeasibility detection", App. C
     eps_infeas: float = 1e-9
+    reduced_costs: int = 0  # 0: proj_R(c - A'y) (Sec. 2); 1: App. A's bound proximity
 
 
 # ----------------------------------------------------------------------------
@@ -471,9 +472,19 @@ def normalized_gap(lp: ScaledLP, x, y, Ax, ATy, x_ref, y_ref, omega):
 # optimality measures on the unscaled LP (R10)
 # ----------------------------------------------------------------------------
 
-def kkt_stats(inst, A_orig, x, y):
+def reduced_costs_bound_proximity(g, x, lv, uv):
+    """App. A's alternative reduced costs: r_i = g_i when g_i > 0 and x_i - lv_i <= |x_i|,
+    or g_i < 0 and uv_i - x_i <= |x_i|; 0 otherwise (g = c - A'y)."""
+    with np.errstate(invalid="ignore"):
+        near_lo = (x - lv) <= np.abs(x)
+        near_hi = (uv - x) <= np.abs(x)
+    return np.where((g > 0) & near_lo, g, np.where((g < 0) & near_hi, g, 0.0))
+
+
+def kkt_stats(inst, A_orig, x, y, reduced_costs=0):
     """Residuals, objectives and gaps of (x, y) for the unscaled LP, with the reduced
-    costs r = proj_R(c - A'y) (Sec. 2, "natural choice").
+    costs r = proj_R(c - A'y) (Sec. 2, "natural choice"), or App. A's bound-proximity
+    choice when ``reduced_costs`` = 1.
 
     primal residual  Ax - proj_[lc,uc](Ax)        relative: /(1 + ||Combine(lc,uc)||_2)
     dual residual    (c - A'y) - r                relative: /(1 + ||c||_2)
@@ -484,7 +495,10 @@ def kkt_stats(inst, A_orig, x, y):
     ATy = A_orig.T @ y
     pres = Ax - proj_box(Ax, inst.lc, inst.uc)
     g = inst.c - ATy
-    r = proj_R(g, inst.lv, inst.uv)
+    if reduced_costs == 1:
+        r = reduced_costs_bound_proximity(g, x, inst.lv, inst.uv)
+    else:
+        r = proj_R(g, inst.lv, inst.uv)
     dres = g - r
     pobj = float(np.dot(inst.c, x))
     dobj = -p_fn(-y, inst.lc, inst.uc) - p_fn(-r, inst.lv, inst.uv)
@@ -742,7 +756,7 @@ def solve(inst, prm: Params | None = None, trace_iters: int = 0, lp: ScaledLP | 
     y = np.zeros(m) if y_init is None else np.array(y_init, dtype=float)
 
     def measures(xs, ys):
-        return kkt_stats(inst, lp.A_orig, lp.d2 * xs, lp.d1 * ys)
+        return kkt_stats(inst, lp.A_orig, lp.d2 * xs, lp.d1 * ys, prm.reduced_costs)
 
     def infeas(cands):
         """Certificate directions are tested on the unscaled LP; a certificate is

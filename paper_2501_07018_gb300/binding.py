@@ -45,6 +45,8 @@ class Params(ctypes.Structure):
         ("profile", ctypes.c_int), ("verbose", ctypes.c_int),
         ("feasibility_polishing", ctypes.c_int), ("polish_log_cap", ctypes.c_int64),
         ("polish_log", ctypes.c_void_p),
+        ("detect_infeasibility", ctypes.c_int), ("eps_infeas", ctypes.c_double),
+        ("reduced_costs", ctypes.c_int),
     ]
 
 

@@ -37,7 +37,7 @@ __device__ __forceinline__ int64_t gs() { return (int64_t)gridDim.x * blockDim.x
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void __launch_bounds__(kThreads)
-    k_kkt(PointRef<T> z, OrigVecs o, int64_t m, int64_t n, KktScratch ks) {
+    k_kkt(PointRef<T> z, OrigVecs o, int64_t m, int64_t n, KktScratch ks, int rc_mode) {
   __shared__ double red[5 * kWarps];
   double v[5] = {0, 0, 0, 0, 0};  // pres2, dres2, pobj, dobj_rows, dobj_cols
   double mx[2] = {0, 0};
@@ -56,11 +56,18 @@ __global__ void __launch_bounds__(kThreads)
     const double x = (double)z.x[j] * o.d2[j];
     const double aty = (double)z.aty[j] * o.inv_d2[j];
     const double g = o.c[j] - aty;
-    const bool lf = isfinite(o.lv[j]), uf = isfinite(o.uv[j]);
-    double r = g;
-    if (lf && !uf) r = fmax(g, 0.0);
-    if (!lf && uf) r = fmin(g, 0.0);
-    if (!lf && !uf) r = 0.0;
+    double r;
+    if (rc_mode == 1) {
+      // App. A: the reduced cost is kept only next to the bound it prices (relative to |x|)
+      const bool near_lo = x - o.lv[j] <= fabs(x), near_hi = o.uv[j] - x <= fabs(x);
+      r = (g > 0.0 && near_lo) ? g : ((g < 0.0 && near_hi) ? g : 0.0);
+    } else {
+      const bool lf = isfinite(o.lv[j]), uf = isfinite(o.uv[j]);
+      r = g;
+      if (lf && !uf) r = fmax(g, 0.0);
+      if (!lf && uf) r = fmin(g, 0.0);
+      if (!lf && !uf) r = 0.0;
+    }
     const double dr = g - r;
     v[1] += dr * dr;
     mx[1] = fmax(mx[1], fabs(dr));
@@ -115,7 +122,7 @@ __global__ void __launch_bounds__(kThreads)
 template <class T>
 void launch_kkt(const PointRef<T>& z, const OrigVecs& o, int64_t m, int64_t n,
                 const KktScratch& ks, cudaStream_t s) {
-  k_kkt<T><<<ks.grid, kThreads, 0, s>>>(z, o, m, n, ks);
+  k_kkt<T><<<ks.grid, kThreads, 0, s>>>(z, o, m, n, ks, ks.rc_mode);
   PDLP_LAUNCH_CHECK();
 }
 

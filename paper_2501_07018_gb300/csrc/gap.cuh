@@ -52,6 +52,7 @@ struct KktScratch {
   unsigned int* counter;
   KktSums* out;
   int grid;
+  int rc_mode = 0;  // reduced costs: 0 proj_R(c - A'y) (Sec. 2), 1 App. A's bound proximity
 };
 template <class T>
 void launch_kkt(const PointRef<T>& z, const OrigVecs& o, int64_t m, int64_t n,

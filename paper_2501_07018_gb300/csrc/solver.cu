@@ -19,6 +19,7 @@
 
 #include "../../include/pdlp.h"
 #include "gap.cuh"
+#include "infeas.cuh"
 #include "pdhg.cuh"
 
 namespace pdlp {
@@ -152,9 +153,10 @@ __global__ void k_copy2(const T* a, T* a_out, int64_t na, const T* b, T* b_out, 
 template <class T>
 __global__ void k_unscale(const T* x, const T* y, const double* d1, const double* d2,
                           const double* lv, const double* uv, const int32_t* perm_r,
-                          const int32_t* perm_c, double* xo, double* yo, int64_t m, int64_t n) {
+                          const int32_t* perm_c, double* xo, double* yo, int64_t m, int64_t n,
+                          bool clamp) {
   for (int64_t j = sgi(); j < n; j += sgs())
-    xo[perm_c[j]] = fmin(fmax(d2[j] * (double)x[j], lv[j]), uv[j]);
+    xo[perm_c[j]] = clamp ? fmin(fmax(d2[j] * (double)x[j], lv[j]), uv[j]) : d2[j] * (double)x[j];
   for (int64_t i = sgi(); i < m; i += sgs()) yo[perm_r[i]] = d1[i] * (double)y[i];
 }
 
@@ -502,7 +504,7 @@ static bool goal_met(const KktResult& r, const pdlp_params& p, int goal) {
   return converged(r, p);
 }
 
-enum RunOutcome { kRunDone, kRunLimit, kRunError, kRunTime, kRunPaused };
+enum RunOutcome { kRunDone, kRunLimit, kRunError, kRunTime, kRunPaused, kRunPrimalInf, kRunDualInf };
 
 // One PDLP run (Algorithm 1) on the device: its iterate slots and running sums, the
 // LP vectors it solves, z^{n,0}, the device-side scalars and the host-side restart
@@ -516,6 +518,7 @@ struct Run {
   int goal = kGoalOptimal;
   int64_t max_iters = 0;
   bool trace = false;
+  bool infeas = false;  // infeasibility detection at the checks (normal PDLP only)
   bool started = false, have_mu_ref = false;
   double mu_ref = 0.0, mu_c_prev = INFINITY;
   int64_t k = 0, t = 0, attempts_at_last = 0;
@@ -561,6 +564,8 @@ struct Solver {
   double* dist_out = nullptr;
   double* step_tab = nullptr;  // Algorithm 2's factors by accepted count (StepTable)
   int64_t step_len = 0;
+  InfeasScratch<T> isc{};      // infeasibility detection (Sec. 3, App. C)
+  bool ray_output = false;     // the returned x is a dual-infeasibility ray (no clamp)
   EventTimer timer;
   GapStats gap_stats;
   int64_t launches = 0;
@@ -591,6 +596,7 @@ struct Solver {
     counters = arena.alloc<unsigned int>(8);
     PDLP_CUDA_CHECK(cudaMemsetAsync(counters, 0, 8 * sizeof(unsigned int), s));
     kks.grid = g_red;
+    kks.rc_mode = prm.reduced_costs;
     kks.part = arena.alloc<double>(7 * (int64_t)g_red);
     kks.counter = counters + 1;
     kks.out = arena.alloc<KktSums>(1);
@@ -647,6 +653,53 @@ struct Solver {
     Yk = arena.alloc<T>(m);
     Yt = arena.alloc<T>(m);
     AXt = arena.alloc<T>(m);
+  }
+
+  void alloc_infeas() {
+    const int64_t m = P.m, n = P.n;
+    isc.yd = arena.alloc<T>(m);
+    isc.atyd = arena.alloc<T>(n);
+    isc.xb = arena.alloc<T>(3 * n);
+    isc.axb = arena.alloc<T>(3 * m);
+    isc.grid = g_red;
+    isc.part = arena.alloc<double>(15 * (int64_t)g_red);
+    isc.counter = counters + 4;
+    isc.out = arena.alloc<double>(15);
+  }
+
+  // App. C's tests on the three candidates of this check (difference of the last two
+  // iterates, current iterate, average in Xa..ATYa); on success out_pt is the returned
+  // point: (current x, certificate y) or (certificate x, current y).
+  int check_infeasibility(Run<T>& r, PointRef<T>& out_pt, KktResult& out_k) {
+    const int64_t m = P.m, n = P.n;
+    const int cur = r.hs.cur;
+    const InfeasInputs<T> in{r.b.X[cur], r.b.Y[cur], r.b.ATY[cur], r.b.X[cur ^ 1], r.b.Y[cur ^ 1],
+                             Xa, Ya, ATYa, r.b.lc, r.b.uc, r.b.lv, r.b.uv};
+    int nl = 0;
+    const auto t0 = Clock::now();
+    const InfeasMeasures im = infeasibility_measures<T>(in, isc, origv(), P.A, P.AT, g_plain_a,
+                                                        g_plain_at, m, n, s, &nl);
+    launches += nl;
+    ms_checks += 1e3 * secs_since(t0);
+    const double eps = prm.eps_infeas;
+    const T* ys[3] = {isc.yd, r.b.Y[cur], Ya};
+    const T* atys[3] = {isc.atyd, r.b.ATY[cur], ATYa};
+    for (int c = 0; c < 3; ++c) {
+      if (im.y_obj[c] > 0.0 && im.y_res[c] <= eps * im.y_obj[c]) {
+        out_pt = PointRef<T>{r.b.X[cur], ys[c], r.b.AX[cur], atys[c]};
+        out_k = kkt(out_pt);
+        return PDLP_PRIMAL_INFEASIBLE;
+      }
+    }
+    for (int c = 0; c < 3; ++c) {
+      if (im.cx[c] < 0.0 && im.x_res[c] <= eps * std::fabs(im.cx[c])) {
+        out_pt = PointRef<T>{isc.xb + c * n, r.b.Y[cur], isc.axb + c * m, r.b.ATY[cur]};
+        out_k = kkt(out_pt);
+        ray_output = true;
+        return PDLP_DUAL_INFEASIBLE;
+      }
+    }
+    return 0;
   }
 
   void zero_sums(Run<T>& r) {
@@ -864,6 +917,11 @@ struct Solver {
           out_pt = cand;
           return kRunDone;
         }
+        if (r.infeas) {  // after the termination test, before the restart decision
+          const int inf = check_infeasibility(r, out_pt, out_k);
+          if (inf == PDLP_PRIMAL_INFEASIBLE) return kRunPrimalInf;
+          if (inf == PDLP_DUAL_INFEASIBLE) return kRunDualInf;
+        }
         if (is_limit) {
           out_pt = cand;
           return kRunLimit;
@@ -954,6 +1012,8 @@ struct Solver {
       case kRunDone: return PDLP_OPTIMAL;
       case kRunLimit: return PDLP_ITERATION_LIMIT;
       case kRunTime: return PDLP_TIME_LIMIT;
+      case kRunPrimalInf: return PDLP_PRIMAL_INFEASIBLE;
+      case kRunDualInf: return PDLP_DUAL_INFEASIBLE;
       default: return PDLP_NUMERICAL_ERROR;
     }
   }
@@ -1088,7 +1148,8 @@ struct Solver {
   void emit(const Problem<U>& Q, const PointRef<U>& pt, double* xo, double* yo) {
     const int64_t m = Q.m, n = Q.n;
     k_unscale<U><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(
-        pt.x, pt.y, Q.d1, Q.d2, Q.orig.lv, Q.orig.uv, Q.perm_r, Q.perm_c, xo, yo, m, n);
+        pt.x, pt.y, Q.d1, Q.d2, Q.orig.lv, Q.orig.uv, Q.perm_r, Q.perm_c, xo, yo, m, n,
+        !ray_output);
     PDLP_LAUNCH_CHECK();
     launches++;
   }
@@ -1111,6 +1172,7 @@ struct Solver {
     alloc_shared();
     alloc_run(main_run);
     if (prm.feasibility_polishing && std::is_same<T, double>::value) alloc_polishing();
+    if (prm.detect_infeasibility) alloc_infeas();
     const int64_t m = P.m, n = P.n;
 
     const double eta0 = P.max_abs > 0.0 ? 1.0 / P.max_abs : 1.0;
@@ -1119,6 +1181,7 @@ struct Solver {
     start_run(main_run, nullptr, nullptr, omega0, eta0, prm.max_iters, kGoalOptimal, P.c, P.lc,
               P.uc, P.lv, P.uv);
     main_run.trace = true;
+    main_run.infeas = prm.detect_infeasibility != 0;
     PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
     const double t_setup = secs_since(t_start);
     t_solve0 = Clock::now();
@@ -1298,6 +1361,9 @@ void pdlp_params_default(pdlp_params* p) {
   p->profile = 0;
   p->verbose = 0;
   p->feasibility_polishing = 0;
+  p->detect_infeasibility = 1;
+  p->eps_infeas = 1e-9;
+  p->reduced_costs = 0;
   p->polish_log_cap = 0;
   p->polish_log = nullptr;
 }
@@ -1464,6 +1530,7 @@ int pdlp_kkt(int64_t m, int64_t n, const pdlp_csr* A, const double* c, const dou
     const int g = std::max(1, num_sms() * 4);
     KktScratch ks;
     ks.grid = g;
+    ks.rc_mode = prm.reduced_costs;
     ks.part = pp.arena.alloc<double>(7 * (int64_t)g);
     ks.counter = pp.arena.alloc<unsigned int>(1);
     ks.out = pp.arena.alloc<KktSums>(1);

@@ -96,3 +96,4 @@ def test_binding_constants_match_header(lib):
         assert int(defs[key]) == code, name
     p = binding.default_params()
     assert p.feasibility_polishing == 0 and p.polish_log_cap == 0 and not p.polish_log
+    assert p.detect_infeasibility == 1 and p.eps_infeas == 1e-9 and p.reduced_costs == 0

@@ -161,15 +161,17 @@ def test_normalized_gap_parity(pkg, name):
         assert abs(got - want) <= 1e-10 * max(abs(want), 1e-300) + 1e-15, (trial, got, want)
 
 
-def test_kkt_parity(pkg):
+@pytest.mark.parametrize("reduced_costs", [0, 1])
+def test_kkt_parity(pkg, reduced_costs):
+    """Optimality measures with Sec. 2's reduced costs and with App. A's variant."""
     inst = GH.edge_instance()
     rng = np.random.default_rng(6)
     A = inst.scipy_csr()
     for _ in range(3):
         x, y = _rand_point(rng, inst)
         got = pkg.kkt(inst.m, inst.n, inst.row_ptr, inst.col_idx, inst.val, inst.c, inst.lc,
-                      inst.uc, inst.lv, inst.uv, x, y)
-        want = O.kkt_stats(inst, A, x, y)
+                      inst.uc, inst.lv, inst.uv, x, y, reduced_costs=reduced_costs)
+        want = O.kkt_stats(inst, A, x, y, reduced_costs=reduced_costs)
         for k in ("rel_kkt", "rel_primal", "rel_dual", "rel_gap", "primal_res_l2", "dual_res_l2",
                   "pobj", "dobj", "paper_gap"):
             assert abs(got[k] - want[k]) <= 1e-11 * max(1.0, abs(want[k])), k

@@ -479,3 +479,46 @@ def test_step_factors_first_step_positive():
     """Algorithm 2's reduction factor must be positive at the first step (R3)."""
     red, grow = O.step_factors(0)
     assert red == pytest.approx(1 - 2 ** -0.3) and grow == pytest.approx(1 + 2 ** -0.6)
+
+
+def test_app_a_reduced_costs_closed_forms():
+    """App. A: keep c_i - a_i'y only next to the bound it prices, measured against
+    |x_i|.  Hand cases, and the golden LP's optimum, where complementary slackness makes
+    both choices coincide (all measures ~0)."""
+    g = np.array([-2.0, 3.0, 3.0, -1.0, 4.0])
+    x = np.array([0.5, 0.5, -5.0, 9.0, 2.0])
+    lv = np.array([0.0, 0.0, -np.inf, 0.0, 2.0])
+    uv = np.array([1e12, 1e12, np.inf, 10.0, 2.0])
+    r = O.reduced_costs_bound_proximity(g, x, lv, uv)
+    # far from the huge upper bound: 0; near the lower bound: kept; free: 0;
+    # upper bound 1 away from x = 9 (<= |x|): kept; fixed at 2: kept
+    np.testing.assert_array_equal(r, [0.0, 3.0, 0.0, -1.0, 4.0])
+    with open(os.path.join(GOLDEN, "textbook_lp.json")) as f:
+        gold = json.load(f)
+    inf = float("inf")
+    conv = lambda v: [inf if s == "inf" else (-inf if s == "-inf" else s) for s in v]  # noqa
+    inst = H.make_lp(gold["A"], gold["c"], conv(gold["lc"]), conv(gold["uc"]), conv(gold["lv"]),
+                     conv(gold["uv"]))
+    st = O.kkt_stats(inst, inst.scipy_csr(), np.array(gold["x_star"]), np.array(gold["y_star"]),
+                     reduced_costs=1)
+    assert st["rel_kkt"] <= 1e-12
+
+
+def test_app_a_reduced_costs_huge_bound():
+    """A variable with a huge, inactive upper bound: the natural reduced cost prices it
+    at 1e12 and wrecks the dual objective; App. A's choice ignores it."""
+    inst = H.make_lp([[1.0, 1.0]], [1.0, 2.0], [1.0], [1.0], [0.0, 0.0], [1e12, 1e12])
+    x = np.array([1.0, 0.0])
+    y = np.array([1.0 + 1e-9])  # slightly off the optimal multiplier 1
+    nat = O.kkt_stats(inst, inst.scipy_csr(), x, y)
+    app = O.kkt_stats(inst, inst.scipy_csr(), x, y, reduced_costs=1)
+    assert nat["rel_gap"] > 1e-4      # -1e-9 * 1e12 enters the dual objective
+    assert app["rel_kkt"] <= 1e-8
+
+
+def test_app_a_reduced_costs_same_optimum():
+    inst = lpgen.config0()
+    a = O.solve(inst, O.Params(eps_rel_kkt=1e-8))
+    b = O.solve(inst, O.Params(eps_rel_kkt=1e-8, reduced_costs=1))
+    assert a.status == b.status == O.OPTIMAL
+    assert abs(a.stats["pobj"] - b.stats["pobj"]) <= 1e-6 * abs(a.stats["pobj"])
