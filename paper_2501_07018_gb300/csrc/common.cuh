@@ -106,6 +106,44 @@ __device__ __forceinline__ double block_sum_array(const double* partials, int co
   return v[0];
 }
 
+// Totals of per-CTA partials by one CTA: KS arrays to sum, then KM arrays of
+// non-negative values to take the maximum of, each `count` long, stored one after the
+// other from `part`.  Every thread reads its strided elements of all arrays (L2 loads,
+// issued together), then fixed-order block trees; results valid in thread 0.  The
+// partials must have been made visible (last_block_arrival).
+template <int KS, int KM, int NW = kWarps>
+__device__ __forceinline__ void block_reduce_partials(const double* part, int count,
+                                                      double (&sums)[KS], double (&maxs)[KM],
+                                                      double* sm_sum, double* sm_max) {
+#pragma unroll
+  for (int k = 0; k < KS; ++k) sums[k] = 0.0;
+#pragma unroll
+  for (int k = 0; k < KM; ++k) maxs[k] = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < KS; ++k) sums[k] += __ldcg(part + (size_t)k * count + i);
+#pragma unroll
+    for (int k = 0; k < KM; ++k) maxs[k] = fmax(maxs[k], __ldcg(part + (size_t)(KS + k) * count + i));
+  }
+  block_sum<KS, NW>(sums, sm_sum);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < KM; ++k) {
+    const double w = warp_max(maxs[k]);
+    if (lane == 0) sm_max[k * NW + warp] = w;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+      double a = 0.0;
+      for (int w = 0; w < NW; ++w) a = fmax(a, sm_max[k * NW + w]);
+      maxs[k] = a;
+    }
+  }
+  __syncthreads();
+}
+
 // Sums each of K arrays partials[k*count .. k*count+count) by one CTA in a single
 // pass: a group of blockDim/K threads (a power of two <= 32) per array reads it
 // strided, then shuffles; every thread of the group holds the result.  The order is

@@ -99,14 +99,10 @@ __global__ void __launch_bounds__(kThreads)
     ks.part[6 * G + blockIdx.x] = b;
   }
   if (!last_block_arrival(ks.counter)) return;
-  double tot[5];
-  for (int k = 0; k < 5; ++k) tot[k] = block_sum_array(ks.part + k * G, G, red);
+  double tot[5], mxt[2];
+  block_reduce_partials<5, 2>(ks.part, G, tot, mxt, red, mred);
   if (threadIdx.x == 0) {
-    double a = 0, b = 0;
-    for (int i = 0; i < G; ++i) {
-      a = fmax(a, ((volatile double*)ks.part)[5 * G + i]);
-      b = fmax(b, ((volatile double*)ks.part)[6 * G + i]);
-    }
+    const double a = mxt[0], b = mxt[1];
     KktSums r;
     r.pres2 = tot[0];
     r.dres2 = tot[1];

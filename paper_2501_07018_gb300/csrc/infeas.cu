@@ -45,25 +45,50 @@ __device__ __forceinline__ double proj_sbar(double v, bool lf, bool uf) {
   return v;
 }
 
+// The projected candidates and, per candidate, c'x-bar (unscaled): the dual test needs
+// c'x-bar < 0, so the A-side products are formed only for candidates that pass it.
 template <class T>
-__global__ void k_infeas_prep(InfeasInputs<T> in, InfeasScratch<T> sc, int64_t m, int64_t n) {
+__global__ void __launch_bounds__(kThreads)
+    k_infeas_prep(InfeasInputs<T> in, InfeasScratch<T> sc, OrigVecs o, int64_t m, int64_t n) {
+  __shared__ double red[3 * kWarps];
+  __shared__ double mred[1];
   for (int64_t i = gi(); i < m; i += gs()) {
     const bool lf = isfinite(in.lc[i]), uf = isfinite(in.uc[i]);
     sc.yd[i] = (T)proj_y((double)in.y[i] - (double)in.y_prev[i], lf, uf);
   }
+  double v[3] = {0.0, 0.0, 0.0};
   for (int64_t j = gi(); j < n; j += gs()) {
     const bool lf = isfinite(in.lv[j]), uf = isfinite(in.uv[j]);
-    sc.xb[j] = (T)proj_xbar((double)in.x[j] - (double)in.x_prev[j], lf, uf);
-    sc.xb[n + j] = (T)proj_xbar((double)in.x[j], lf, uf);
-    sc.xb[2 * n + j] = (T)proj_xbar((double)in.xa[j], lf, uf);
+    const T a = (T)proj_xbar((double)in.x[j] - (double)in.x_prev[j], lf, uf);
+    const T b = (T)proj_xbar((double)in.x[j], lf, uf);
+    const T c = (T)proj_xbar((double)in.xa[j], lf, uf);
+    sc.xb[j] = a;
+    sc.xb[n + j] = b;
+    sc.xb[2 * n + j] = c;
+    const double w = o.c[j] * o.d2[j];
+    v[0] += w * (double)a;
+    v[1] += w * (double)b;
+    v[2] += w * (double)c;
   }
+  block_sum<3>(v, red);
+  const int G = gridDim.x;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 3; ++k) sc.part[k * G + blockIdx.x] = v[k];
+    sc.part[3 * G + blockIdx.x] = 0.0;  // (no maximum is taken here)
+  }
+  if (!last_block_arrival(sc.counter)) return;
+  double tot[3], unused[1];
+  block_reduce_partials<3, 1>(sc.part, G, tot, unused, red, mred);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 3; ++k) sc.out[15 + k] = tot[k];
 }
 
 // 9 sums (y-objective rows, y-objective columns, c'x-bar per candidate) and 6 maxima
 // (||A'y + r||_inf, ||A x + s||_inf per candidate); per-CTA partials, fixed-order total
 template <class T>
 __global__ void __launch_bounds__(kThreads)
-    k_infeas_reduce(InfeasInputs<T> in, InfeasScratch<T> sc, OrigVecs o, int64_t m, int64_t n) {
+    k_infeas_reduce(InfeasInputs<T> in, InfeasScratch<T> sc, OrigVecs o, int64_t m, int64_t n,
+                    unsigned xmask) {
   __shared__ double red[9 * kWarps];
   __shared__ double mred[6 * kWarps];
   const T* yc[3] = {sc.yd, in.y, in.ya};
@@ -80,8 +105,10 @@ __global__ void __launch_bounds__(kThreads)
         v[c] += l * y;
       else if (y < 0.0)
         v[c] += u * y;
-      const double p = (double)sc.axb[c * m + i] * o.inv_d1[i];
-      mx[3 + c] = fmax(mx[3 + c], fabs(p + proj_sbar(-p, lf, uf)));
+      if (xmask & (1u << c)) {  // A x-bar formed for this candidate
+        const double p = (double)sc.axb[c * m + i] * o.inv_d1[i];
+        mx[3 + c] = fmax(mx[3 + c], fabs(p + proj_sbar(-p, lf, uf)));
+      }
     }
   }
   for (int64_t j = gi(); j < n; j += gs()) {
@@ -117,15 +144,11 @@ __global__ void __launch_bounds__(kThreads)
     }
   }
   if (!last_block_arrival(sc.counter)) return;
-  double tot[15];
-  for (int k = 0; k < 9; ++k) tot[k] = block_sum_array(sc.part + k * G, G, red);
+  double tot[9], mxt[6];
+  block_reduce_partials<9, 6>(sc.part, G, tot, mxt, red, mred);
   if (threadIdx.x == 0) {
-    for (int k = 0; k < 6; ++k) {
-      double a = 0.0;
-      for (int b = 0; b < G; ++b) a = fmax(a, __ldcg(sc.part + (9 + k) * G + b));
-      tot[9 + k] = a;
-    }
-    for (int k = 0; k < 15; ++k) sc.out[k] = tot[k];
+    for (int k = 0; k < 9; ++k) sc.out[k] = tot[k];
+    for (int k = 0; k < 6; ++k) sc.out[9 + k] = mxt[k];
   }
 }
 
@@ -138,13 +161,23 @@ InfeasMeasures infeasibility_measures(const InfeasInputs<T>& in, const InfeasScr
                                       cudaStream_t s, int* launches) {
   const int64_t need = (std::max(m, n) + kThreads - 1) / kThreads;
   const int g = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 8));
-  k_infeas_prep<T><<<g, kThreads, 0, s>>>(in, sc, m, n);
+  k_infeas_prep<T><<<std::min(g, sc.grid), kThreads, 0, s>>>(in, sc, o, m, n);
   PDLP_LAUNCH_CHECK();
   launch_spmv_plain<T>(AT, sc.yd, sc.atyd, grid_at, s);
-  for (int c = 0; c < 3; ++c) launch_spmv_plain<T>(A, sc.xb + c * n, sc.axb + c * m, grid_a, s);
-  k_infeas_reduce<T><<<sc.grid, kThreads, 0, s>>>(in, sc, o, m, n);
+  double cx0[3];
+  PDLP_CUDA_CHECK(cudaMemcpyAsync(cx0, sc.out + 15, sizeof(cx0), cudaMemcpyDeviceToHost, s));
+  PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+  unsigned xmask = 0;
+  int nl = 2;
+  for (int c = 0; c < 3; ++c) {
+    if (!(cx0[c] < 0.0)) continue;
+    launch_spmv_plain<T>(A, sc.xb + c * n, sc.axb + c * m, grid_a, s);
+    xmask |= 1u << c;
+    ++nl;
+  }
+  k_infeas_reduce<T><<<sc.grid, kThreads, 0, s>>>(in, sc, o, m, n, xmask);
   PDLP_LAUNCH_CHECK();
-  if (launches) *launches += 6;
+  if (launches) *launches += nl + 1;
   double h[15];
   PDLP_CUDA_CHECK(cudaMemcpyAsync(h, sc.out, sizeof(h), cudaMemcpyDeviceToHost, s));
   PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
@@ -153,7 +186,8 @@ InfeasMeasures infeasibility_measures(const InfeasInputs<T>& in, const InfeasScr
     r.y_obj[c] = h[c] + h[3 + c];
     r.cx[c] = h[6 + c];
     r.y_res[c] = h[9 + c];
-    r.x_res[c] = h[12 + c];
+    // a candidate without its product cannot pass the dual test (c'x-bar >= 0)
+    r.x_res[c] = (xmask >> c) & 1u ? h[12 + c] : INFINITY;
   }
   return r;
 }

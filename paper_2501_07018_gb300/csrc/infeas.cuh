@@ -20,7 +20,8 @@ struct InfeasInputs {
 
 // Work vectors: yd = proj_Y(y - y_prev) [m] and atyd = A~'yd [n]; xb = the three x
 // candidates projected onto X-bar [3n] and axb = their A~ products [3m]; reduction
-// partials [15 * grid], counter (0 between launches) and the 15 results.
+// partials [15 * grid], counter (0 between launches) and the results [18]: 15 measures,
+// then c'x-bar of the three x candidates from the projection pass.
 template <class T>
 struct InfeasScratch {
   T* yd;

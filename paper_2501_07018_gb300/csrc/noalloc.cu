@@ -90,17 +90,12 @@ __global__ void __launch_bounds__(kThreads)
     part[8 * G + blockIdx.x] = b;
   }
   if (!last_block_arrival(counter)) return;
-  double tot[7];
-  for (int k = 0; k < 7; ++k) tot[k] = block_sum_array(part + k * G, G, red);
+  double tot[7], mxt[2];
+  block_reduce_partials<7, 2>(part, G, tot, mxt, red, mred);
   if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-    for (int i = 0; i < G; ++i) {
-      a = fmax(a, ((volatile double*)part)[7 * G + i]);
-      b = fmax(b, ((volatile double*)part)[8 * G + i]);
-    }
     for (int k = 0; k < 7; ++k) result[k] = tot[k];
-    result[7] = a;
-    result[8] = b;
+    result[7] = mxt[0];
+    result[8] = mxt[1];
   }
 }
 

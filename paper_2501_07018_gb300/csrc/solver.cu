@@ -664,7 +664,7 @@ struct Solver {
     isc.grid = g_red;
     isc.part = arena.alloc<double>(15 * (int64_t)g_red);
     isc.counter = counters + 4;
-    isc.out = arena.alloc<double>(15);
+    isc.out = arena.alloc<double>(18);
   }
 
   // App. C's tests on the three candidates of this check (difference of the last two
