@@ -111,10 +111,13 @@ __device__ __forceinline__ double block_sum_array(const double* partials, int co
 // other from `part`.  Every thread reads its strided elements of all arrays (L2 loads,
 // issued together), then fixed-order block trees; results valid in thread 0.  The
 // partials must have been made visible (last_block_arrival).
+// The shared scratch is taken as arrays of the exact sizes KS * NW and KM * NW, so a
+// call with smaller arrays does not compile.
 template <int KS, int KM, int NW = kWarps>
 __device__ __forceinline__ void block_reduce_partials(const double* part, int count,
                                                       double (&sums)[KS], double (&maxs)[KM],
-                                                      double* sm_sum, double* sm_max) {
+                                                      double (&sm_sum)[KS * NW],
+                                                      double (&sm_max)[KM * NW]) {
 #pragma unroll
   for (int k = 0; k < KS; ++k) sums[k] = 0.0;
 #pragma unroll

@@ -51,7 +51,7 @@ template <class T>
 __global__ void __launch_bounds__(kThreads)
     k_infeas_prep(InfeasInputs<T> in, InfeasScratch<T> sc, OrigVecs o, int64_t m, int64_t n) {
   __shared__ double red[3 * kWarps];
-  __shared__ double mred[1];
+  __shared__ double mred[1 * kWarps];  // exact sizes: block_reduce_partials<3, 1>
   for (int64_t i = gi(); i < m; i += gs()) {
     const bool lf = isfinite(in.lc[i]), uf = isfinite(in.uc[i]);
     sc.yd[i] = (T)proj_y((double)in.y[i] - (double)in.y_prev[i], lf, uf);
