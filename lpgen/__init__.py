@@ -207,3 +207,77 @@ def config1(instance: int = 0, scale: float = 1.0) -> LPInstance:
     m = max(8, int(round(2_000_000 * scale)))
     n = max(8, int(round(5_000_000 * scale)))
     return powerlaw_lp(m, n, config_seed(1, instance), name=f"powerlaw-{m}x{n}")
+
+
+def multicommodity_flow_lp(nodes: int, arcs: int, commodities: int, seed: int,
+                           zipf_a: float = 1.3) -> LPInstance:
+    """Multicommodity min-cost flow: a directed graph with ``nodes`` nodes and ``arcs``
+    arcs whose tails are drawn by rank from a Zipf(``zipf_a``) law over a random node
+    order (a few hub nodes own most arcs), heads uniform among the other nodes; one flow
+    variable f_{k,a} >= 0 per commodity k and arc a (column k * arcs + a); rows:
+      * conservation, one per commodity and node (row k * nodes + v):
+            sum_{a out of v} f_{k,a} - sum_{a into v} f_{k,a} = b_{k,v}   (equality)
+      * capacity, one per arc (row commodities * nodes + a):
+            sum_k f_{k,a} <= cap_a                                         (lc = -inf)
+    Costs U[1,100] per arc (shared by the commodities), capacities U[10,1000].  The
+    supplies come from a feasible flow f0_{k,a} = cap_a U[0,1] / commodities
+    (b_k = N f0_k, summing to zero), so the LP is feasible; with nonnegative costs it is
+    bounded.  Draw order: node order, tail ranks, heads, costs, capacities, f0."""
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(nodes)
+    w = np.arange(1, nodes + 1, dtype=np.float64) ** (-zipf_a)
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    ranks = np.minimum(np.searchsorted(cdf, rng.random(arcs), side="right"), nodes - 1)
+    tail = order[ranks]
+    head = rng.integers(0, nodes - 1, arcs)
+    head = head + (head >= tail)  # uniform among the nodes other than the tail
+    cost = rng.uniform(1.0, 100.0, arcs)
+    cap = rng.uniform(10.0, 1000.0, arcs)
+    K = commodities
+    f0 = cap[None, :] * rng.random((K, arcs)) / K
+    # node-arc incidence per commodity: +1 at the tail, -1 at the head
+    b = np.zeros((K, nodes))
+    for k in range(K):
+        b[k] = np.bincount(tail, weights=f0[k], minlength=nodes) - \
+            np.bincount(head, weights=f0[k], minlength=nodes)
+    # CSR rows of the conservation block of one commodity (same pattern for every k):
+    # row v holds the out-arcs of v (+1) and the in-arcs of v (-1), columns increasing
+    ends = np.concatenate([tail, head])
+    arc_of = np.concatenate([np.arange(arcs), np.arange(arcs)])
+    sgn = np.concatenate([np.ones(arcs), -np.ones(arcs)])
+    o = np.lexsort((arc_of, ends))
+    ends, arc_of, sgn = ends[o], arc_of[o], sgn[o]
+    cnt = np.bincount(ends, minlength=nodes).astype(np.int64)
+    m = K * nodes + arcs
+    n = K * arcs
+    nnz = 3 * n
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    row_len = np.concatenate([np.tile(cnt, K), np.full(arcs, K, dtype=np.int64)])
+    np.cumsum(row_len, out=row_ptr[1:])
+    col = np.empty(nnz, dtype=np.int32)
+    val = np.empty(nnz, dtype=np.float64)
+    blk = 2 * arcs
+    for k in range(K):
+        col[k * blk:(k + 1) * blk] = (k * arcs + arc_of).astype(np.int32)
+        val[k * blk:(k + 1) * blk] = sgn
+    # capacity rows: columns a, arcs + a, ..., (K-1) arcs + a
+    cap_cols = (np.arange(K)[None, :] * arcs + np.arange(arcs)[:, None]).reshape(-1)
+    col[K * blk:] = cap_cols.astype(np.int32)
+    val[K * blk:] = 1.0
+    lc = np.concatenate([b.reshape(-1), np.full(arcs, -np.inf)])
+    uc = np.concatenate([b.reshape(-1), cap])
+    c = np.tile(cost, K)
+    x0 = f0.reshape(-1)
+    return LPInstance(m=m, n=n, row_ptr=row_ptr, col_idx=col, val=val, c=c, lc=lc, uc=uc,
+                      lv=np.zeros(n), uv=np.full(n, np.inf),
+                      name=f"mcf nodes={nodes} arcs={arcs} commodities={K}", x0=x0)
+
+
+def config4(scale: float = 1.0, instance: int = 0) -> LPInstance:
+    """The multicommodity-flow LP sized for one GPU's HBM: 2e6 nodes, 2e7 arcs with
+    Zipf(1.3) out-degrees, 50 commodities (m = 1.2e8, n = 1e9, 3e9 nonzeros); ``scale``
+    shrinks nodes and arcs proportionally (same recipe)."""
+    nodes = max(8, int(round(2_000_000 * scale)))
+    arcs = max(16, int(round(20_000_000 * scale)))
+    return multicommodity_flow_lp(nodes, arcs, 50, config_seed(4, instance))

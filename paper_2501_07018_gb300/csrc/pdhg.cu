@@ -28,6 +28,15 @@ __device__ __forceinline__ long long dkey(double v) {
   const long long b = __double_as_longlong(v);
   return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
 }
+// Sign tests of a non-NaN double on the integer pipe: v < 0 (-0 excluded) and v > 0.
+__device__ __forceinline__ bool neg_strict(double v) {
+  const long long b = __double_as_longlong(v);
+  return b < 0 && b != (long long)0x8000000000000000ULL;
+}
+__device__ __forceinline__ bool pos_strict(double v) { return __double_as_longlong(v) > 0; }
+__device__ __forceinline__ bool neg_strict(float v) { return v < 0.0f; }
+__device__ __forceinline__ bool pos_strict(float v) { return v > 0.0f; }
+
 template <class T>
 __device__ __forceinline__ T clampv(T v, T lo, T hi);
 template <>
@@ -175,7 +184,7 @@ __device__ __forceinline__ void row_epilogue(const EpiCtx<T>& e, const EpiIn<T>&
     // 0); one rounding each and exact in sign
     const T tu = fma(e.sigma, in.d, yh);
     const T tl = fma(e.sigma, in.c, yh);
-    const T yn = tu < (T)0 ? tu : (tl > (T)0 ? tl : (T)0);
+    const T yn = neg_strict(tu) ? tu : (pos_strict(tl) ? tl : (T)0);
     e.out0[row] = v;
     e.out1[row] = yn;
     const A dy = (A)yn - (A)yo;

@@ -47,7 +47,7 @@ def _trace_parity(pkg, inst, iters=100, **prm):
     return res, ora, errs
 
 
-@pytest.mark.parametrize("name", ["config0", "edge", "edge_long", "powerlaw"])
+@pytest.mark.parametrize("name", ["config0", "edge", "edge_long", "powerlaw", "mcf"])
 def test_trace_parity_first_100_iterations(pkg, name):
     """Iterates, accepted steps and restart decisions of the first 100 iterations.
     ``edge_long`` has a row of A and a row of A' that span several chunks of the
@@ -59,6 +59,8 @@ def test_trace_parity_first_100_iterations(pkg, name):
     elif name == "edge_long":
         inst = GH.edge_instance(seed=12, m=12000, n=24000, dense_row_nnz=20000,
                                 dense_col_nnz=10000)
+    elif name == "mcf":  # multicommodity flow: equality and capacity rows, hub rows of A
+        inst = lpgen.multicommodity_flow_lp(200, 2000, 10, seed=7)
     else:
         inst = lpgen.config1(scale=0.002)
     res, ora, errs = _trace_parity(pkg, inst)

@@ -54,6 +54,8 @@ def _instance(name):
         return H.lp_with_feasible_pair(np.random.default_rng(21), 300, 500, density=0.05)[0]
     if name == "edge":
         return GH.edge_instance()
+    if name == "mcf":  # multicommodity flow, 10 commodities on 200 nodes / 2000 arcs
+        return lpgen.multicommodity_flow_lp(200, 2000, 10, seed=7)
     return lpgen.config1(scale=0.0005)  # 1000 x 2500, the bench recipe (HiGHS in ~1 s)
 
 
@@ -115,7 +117,7 @@ def test_polishing_trajectory_parity(pkg, name):
     assert np.array_equal(again.x, got.x) and np.array_equal(again.y, got.y)
 
 
-@pytest.mark.parametrize("name", ["config0", "mixed_bounds", "edge", "powerlaw"])
+@pytest.mark.parametrize("name", ["config0", "mixed_bounds", "edge", "powerlaw", "mcf"])
 def test_polished_solve_meets_paper_criteria(pkg, name):
     inst = _instance(name)
     got = pkg.solve_instance(inst, device=True, feasibility_polishing=1, **CRIT)
