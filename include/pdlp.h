@@ -237,6 +237,30 @@ int pdlp_kkt_products_noalloc(int64_t m, int64_t n, const double* c, const doubl
                               const double* x, const double* y, const double* ax,
                               const double* aty, void* cuda_stream, double* out);
 
+/* One LP of a batch: the arguments of pdlp_solve, outputs included. */
+typedef struct {
+  int64_t m, n;
+  pdlp_csr A;
+  const double *c, *lc, *uc, *lv, *uv;
+  double* x_out; /* [n] */
+  double* y_out; /* [m] */
+} pdlp_problem;
+
+/* Solves `count` independent LPs of any sizes (a batch, e.g. many small LPs that one
+ * solve alone cannot fill the GPU with): each LP runs the whole method of pdlp_solve --
+ * its own step sizes (Algorithm 2), primal weight (Algorithm 3), restarts and
+ * termination -- with the parameters *p for every LP.  `concurrency` LPs (<= 0: 16) are
+ * in flight at once, each on its own CUDA stream driven by its own host thread, on the
+ * calling thread's current device; device memory is allocated stream-ordered, so the
+ * solves do not synchronise one another.  params->inputs_on_device selects host or
+ * device arrays for every problem; params->cuda_stream, trace and polish-log outputs
+ * are ignored.  status_out[count] receives each LP's pdlp_solve return value and
+ * stats_out[count] (may be NULL) its statistics.  Returns 0 when every LP was attempted
+ * (see status_out; pdlp_last_error() then describes the first LP that returned a
+ * negative code), PDLP_INVALID_ARGUMENT for bad arguments of the call itself. */
+int pdlp_solve_batch(int64_t count, const pdlp_problem* problems, const pdlp_params* p,
+                     int concurrency, int* status_out, pdlp_stats* stats_out);
+
 /* Message for the last nonzero return of a call made by this thread. */
 const char* pdlp_last_error(void);
 

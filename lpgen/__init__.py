@@ -281,3 +281,22 @@ def config4(scale: float = 1.0, instance: int = 0) -> LPInstance:
     nodes = max(8, int(round(2_000_000 * scale)))
     arcs = max(16, int(round(20_000_000 * scale)))
     return multicommodity_flow_lp(nodes, arcs, 50, config_seed(4, instance))
+
+
+def uneven_lp(seed: int, m_lo: int = 500, m_hi: int = 20000) -> LPInstance:
+    """One LP of the batch of uneven sizes: m ~ U{m_lo..m_hi}, n ~ U{1.5m..3m}, each
+    column with U{4..12} N(0,1) entries at distinct uniform rows, otherwise the 200 x 400
+    recipe (x0 ~ U[0,10], bounds [0,10], rows A x0 -/+ U[0,1], 30% equalities,
+    c ~ U[-1,1]).  Draw order: m, n, column degrees, then as ``random_lp``."""
+    rng = np.random.default_rng(seed)
+    m = int(rng.integers(m_lo, m_hi + 1))
+    n = int(rng.integers(int(1.5 * m), 3 * m + 1))
+    degrees = rng.integers(4, 13, size=n).astype(np.int64)
+    return _assemble(rng, m, n, degrees, _normal_values, eq_frac=0.3, free_frac=0.0,
+                     name=f"uneven m={m} n={n}")
+
+
+def config2(count: int = 1024, instance: int = 0, m_lo: int = 500, m_hi: int = 20000):
+    """The batch of ``count`` LPs of uneven sizes (``uneven_lp`` with per-LP seeds)."""
+    base = config_seed(2, instance) * 4096
+    return [uneven_lp(base + k, m_lo, m_hi) for k in range(count)]

@@ -50,6 +50,13 @@ class Params(ctypes.Structure):
     ]
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("A", Csr),
+                ("c", ctypes.c_void_p), ("lc", ctypes.c_void_p), ("uc", ctypes.c_void_p),
+                ("lv", ctypes.c_void_p), ("uv", ctypes.c_void_p),
+                ("x_out", ctypes.c_void_p), ("y_out", ctypes.c_void_p)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [
         ("status", ctypes.c_int), ("iterations", ctypes.c_int64), ("attempts", ctypes.c_int64),
@@ -117,6 +124,8 @@ def load_library(path: str | None = None):
     lib.pdlp_kkt.restype = ctypes.c_int
     lib.pdlp_kkt_products_noalloc.argtypes = [i64, i64, P, P, P, P, P, P, P, P, P, P, P]
     lib.pdlp_kkt_products_noalloc.restype = ctypes.c_int
+    lib.pdlp_solve_batch.argtypes = [i64, P, ctypes.POINTER(Params), ctypes.c_int, P, P]
+    lib.pdlp_solve_batch.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -278,6 +287,45 @@ def solve_instance(inst, trace_iters: int = 0, device: bool = False, **params) -
 
         arrs = [torch.as_tensor(np.asarray(a)).cuda() for a in arrs]
     return solve(inst.m, inst.n, *arrs, trace_iters=trace_iters, **params)
+
+
+def solve_batch(instances, device: bool = False, concurrency: int = 16, **params) -> list:
+    """pdlp_solve_batch over objects with m, n, row_ptr, col_idx, val, c, lc, uc, lv, uv
+    attributes (host arrays; ``device=True`` stages them as CUDA tensors first).
+    Returns one SolveResult per instance, in order; a negative status does not raise
+    (its message is in ``stats['error']`` of the first failing instance)."""
+    lib = load_library()
+    mh = _Marshal(device)
+    probs = (Problem * max(1, len(instances)))()
+    outs = []
+    for k, inst in enumerate(instances):
+        arrs = [inst.row_ptr, inst.col_idx, inst.val, inst.c, inst.lc, inst.uc, inst.lv, inst.uv]
+        if device:
+            import torch
+
+            arrs = [torch.as_tensor(np.asarray(a)).cuda() for a in arrs]
+        A, vecs = _lp_args(mh, inst.m, inst.n, *arrs)
+        x, xp = mh.out(inst.n)
+        y, yp = mh.out(inst.m)
+        pr = probs[k]
+        pr.m, pr.n, pr.A = inst.m, inst.n, A
+        pr.c, pr.lc, pr.uc, pr.lv, pr.uv = vecs
+        pr.x_out, pr.y_out = xp, yp
+        outs.append((x, y))
+    prm = _params_for(device, params)
+    status = (ctypes.c_int * max(1, len(instances)))()
+    stats = (Stats * max(1, len(instances)))()
+    _check(lib.pdlp_solve_batch(len(instances), ctypes.addressof(probs), ctypes.byref(prm),
+                                int(concurrency), ctypes.addressof(status), ctypes.addressof(stats)))
+    res = []
+    first_error = lib.pdlp_last_error().decode()
+    for k, (x, y) in enumerate(outs):
+        st = stats[k].as_dict()
+        if status[k] < 0 and first_error:
+            st["error"] = first_error
+            first_error = ""
+        res.append(SolveResult(status[k], x, y, st, []))
+    return res
 
 
 def precondition(m, n, row_ptr, col_idx, val, **params):

@@ -80,7 +80,7 @@ def build_library(verbose: bool = False, force: bool = False) -> str:
     if force or jobs or _stale(LIB, objs):
         libdir = _cuda_lib_dir(nvcc)
         tmp = LIB + ".tmp"
-        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "shared",
+        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "shared", "-lpthread",
              "-Xlinker", "-rpath," + libdir])
         os.replace(tmp, LIB)
     return LIB

@@ -13,6 +13,7 @@
 // when the slice started.  Every FP64 instruction thus runs with all 32 lanes active,
 // which matters on GB300 where the FP64 pipe is narrow.  Long rows go in chunks.
 #include <algorithm>
+#include <atomic>
 
 #include "pdhg.cuh"
 
@@ -507,10 +508,12 @@ void fill_step_table(double* f, int64_t len, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 template <class T, int EPI>
 static int spmv_grid_impl(const Mat<T>& M) {
-  static int occ = 0;
+  static std::atomic<int> occ_cache{0};  // same value from every thread
+  int occ = occ_cache.load(std::memory_order_relaxed);
   if (occ == 0) {
     PDLP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv<T, EPI>, kSpmvThreads, 0));
     if (occ < 1) occ = 1;
+    occ_cache.store(occ, std::memory_order_relaxed);
   }
   const int64_t items = (M.work_items() + kSpmvWarps - 1) / kSpmvWarps;  // warps -> CTAs
   const int64_t cap = (int64_t)num_sms() * occ;

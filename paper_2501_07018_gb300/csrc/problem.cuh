@@ -49,14 +49,18 @@ struct Mat {
   int64_t work_items() const { return nchunks + nslices; }
 };
 
-// Simple owning list of device allocations, freed together.
+// Simple owning list of device allocations, freed together.  Allocations are
+// stream-ordered (cudaMallocAsync / cudaFreeAsync on the arena's stream), so that solves
+// running concurrently on different streams never synchronise the device to allocate
+// or free.
 class DeviceArena {
  public:
   ~DeviceArena() { release(); }
+  void set_stream(cudaStream_t s) { stream_ = s; }
   void* alloc_bytes(size_t bytes) {
     void* p = nullptr;
     if (bytes == 0) bytes = 16;
-    PDLP_CUDA_CHECK(cudaMalloc(&p, (bytes + 255) & ~size_t(255)));
+    PDLP_CUDA_CHECK(cudaMallocAsync(&p, (bytes + 255) & ~size_t(255), stream_));
     ptrs_.push_back(p);
     total_ += bytes;
     return p;
@@ -66,7 +70,7 @@ class DeviceArena {
     return static_cast<U*>(alloc_bytes(sizeof(U) * (size_t)(count > 0 ? count : 1)));
   }
   void release() {
-    for (void* p : ptrs_) cudaFree(p);
+    for (void* p : ptrs_) cudaFreeAsync(p, stream_);
     ptrs_.clear();
   }
   size_t total() const { return total_; }
@@ -74,6 +78,7 @@ class DeviceArena {
  private:
   std::vector<void*> ptrs_;
   size_t total_ = 0;
+  cudaStream_t stream_ = nullptr;
 };
 
 // Number of CTAs of the persistent / grid-stride kernels on this device.

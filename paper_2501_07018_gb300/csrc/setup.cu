@@ -2,20 +2,23 @@
 // preconditioning passes of Sec. 3 ("Diagonal Preconditioning") and the row tiling
 // used by the fused SpMV kernels.
 #include <algorithm>
+#include <atomic>
 
 #include "problem.cuh"
 
 namespace pdlp {
 
-static int g_num_sms = 0;
+static std::atomic<int> g_num_sms{0};  // same value from every thread (one GPU model)
 
 int num_sms() {
-  if (g_num_sms == 0) {
+  int v = g_num_sms.load(std::memory_order_relaxed);
+  if (v == 0) {
     int dev = 0;
     PDLP_CUDA_CHECK(cudaGetDevice(&dev));
-    PDLP_CUDA_CHECK(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+    PDLP_CUDA_CHECK(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+    g_num_sms.store(v, std::memory_order_relaxed);
   }
-  return g_num_sms;
+  return v;
 }
 
 int grid_ctas(int per_sm) { return num_sms() * per_sm; }

@@ -8,12 +8,15 @@
 // counts where something else happens -- every check_period accepted iterations
 // (termination and restart evaluation), and whenever restart condition (iii) can fire
 // -- which it computes in advance from (k, t).
+#include <atomic>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
 #include <limits>
 #include <memory>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -577,7 +580,7 @@ struct Solver {
   T *Xk = nullptr, *Yk = nullptr;                          // (x^k, y^k) of the pause
   T *Xt = nullptr, *AXt = nullptr, *Yt = nullptr, *ATYt = nullptr;  // polished pair
 
-  Solver(const pdlp_params& p, cudaStream_t st) : prm(p), s(st) {}
+  Solver(const pdlp_params& p, cudaStream_t st) : prm(p), s(st) { arena.set_stream(st); }
 
   void alloc_shared() {
     const int64_t m = P.m, n = P.n;
@@ -1394,6 +1397,69 @@ int pdlp_solve(int64_t m, int64_t n, const pdlp_csr* A, const double* c, const d
   }
 }
 
+int pdlp_solve_batch(int64_t count, const pdlp_problem* problems, const pdlp_params* p,
+                     int concurrency, int* status_out, pdlp_stats* stats_out) {
+  try {
+    if (count < 0) throw PdlpError(-1, "pdlp_solve_batch: count < 0");
+    if (count > 0 && (!problems || !status_out))
+      throw PdlpError(-1, "pdlp_solve_batch: null problems or status_out");
+    pdlp_params prm;
+    pdlp_params_default(&prm);
+    if (p) prm = *p;
+    prm.trace_iters = 0;
+    prm.trace_out = nullptr;
+    prm.polish_log = nullptr;
+    prm.polish_log_cap = 0;
+    int dev = 0;
+    PDLP_CUDA_CHECK(cudaGetDevice(&dev));
+    const int64_t workers =
+        std::max<int64_t>(1, std::min<int64_t>(concurrency <= 0 ? 16 : concurrency, count));
+    std::atomic<int64_t> next{0};
+    std::mutex mu;
+    std::string first_error;
+    int64_t first_index = -1;
+    auto work = [&]() {
+      cudaStream_t s = nullptr;
+      if (cudaSetDevice(dev) != cudaSuccess ||
+          cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        s = nullptr;
+      }
+      pdlp_params q = prm;
+      q.cuda_stream = s;
+      for (;;) {
+        const int64_t i = next.fetch_add(1);
+        if (i >= count) break;
+        const pdlp_problem& pb = problems[i];
+        int code;
+        if (!s) {
+          set_last_error("pdlp_solve_batch: could not create a stream for a worker");
+          code = PDLP_CUDA_ERROR;
+        } else {
+          code = pdlp_solve(pb.m, pb.n, &pb.A, pb.c, pb.lc, pb.uc, pb.lv, pb.uv, &q, pb.x_out,
+                            pb.y_out, stats_out ? &stats_out[i] : nullptr);
+        }
+        status_out[i] = code;
+        if (code < 0) {
+          std::lock_guard<std::mutex> lock(mu);
+          if (first_index < 0 || i < first_index) {
+            first_index = i;
+            first_error = std::string("problem ") + std::to_string(i) + ": " + pdlp_last_error();
+          }
+        }
+      }
+      if (s) cudaStreamDestroy(s);
+    };
+    std::vector<std::thread> pool;
+    for (int64_t w = 1; w < workers; ++w) pool.emplace_back(work);
+    work();
+    for (auto& t : pool) t.join();
+    if (first_index >= 0) set_last_error(first_error);
+    return 0;
+  } catch (...) {
+    return handle_exception();
+  }
+}
+
 int pdlp_precondition(int64_t m, int64_t n, const pdlp_csr* A, const pdlp_params* p,
                       double* d1_out, double* d2_out, double* scaled_val_out) {
   try {
@@ -1406,6 +1472,7 @@ int pdlp_precondition(int64_t m, int64_t n, const pdlp_csr* A, const pdlp_params
     StreamGuard sg(prm.cuda_stream);
     cudaStream_t s = sg.s;
     DeviceArena arena;
+    arena.set_stream(s);
     // stage the matrix from its own memory space and the placeholder vectors from host
     Inputs mat = in;
     DevInputs d;
@@ -1452,6 +1519,7 @@ struct PointProblem {
 static void stage_point_problem(PointProblem& pp, const Inputs& in, const double* x,
                                 const double* y, const double* xr, const double* yr,
                                 cudaStream_t s) {
+  pp.arena.set_stream(s);
   DevInputs d = stage_inputs(pp.arena, in, s);
   validate(pp.arena, in, d, s);
   build_problem<double>(pp.arena, in, d, 0, 0.0, pp.P, s);
