@@ -70,6 +70,11 @@ used):
       s = proj_Sbar(-Ax); the tests run on the unscaled LP.  The returned point is
       (current x, certificate y) for primal infeasibility and (certificate x, current
       y) for dual infeasibility.
+  R23 The differentiated map is K steps of Eq. (3) on the LP as given (no
+      preconditioning, restarts or adaptive steps: the step sizes are inputs), from
+      R1's start, with the dual step of R17/R18; at a clamp boundary (u = lv, yh =
+      -sigma uc, ...) the derivative of the inside branch is taken as 0 for the
+      iterate (measure-zero set).
 """
 from __future__ import annotations
 
@@ -865,3 +870,78 @@ def _solve_polished(lp, prm: Params, run: PdlpRun, measures):
         if converged(measures(x_t, y_t), prm):
             entry["accepted"] = True
             return OPTIMAL, x_t, y_t, log
+
+
+# ----------------------------------------------------------------------------
+# differentiation of unrolled PDHG (the adjoint of K steps of Eq. (3))
+# ----------------------------------------------------------------------------
+
+def unrolled_pdhg(inst, K, eta, omega):
+    """K steps of PDHG, Eq. (3), on the LP as given (no preconditioning, restarts or
+    adaptive steps): constant tau = eta/omega, sigma = eta*omega, start (proj_X(0), 0)
+    (R1), dual step in the form of R17 with A x' - A x by linearity (R18).  Returns the
+    list of iterates (x_k, y_k, Ax_k, A'y_k), k = 0..K (R23)."""
+    A = inst.scipy_csr()
+    AT = A.T.tocsr()
+    tau, sigma = eta / omega, eta * omega
+    x = proj_box(np.zeros(inst.n), inst.lv, inst.uv)
+    y = np.zeros(inst.m)
+    Ax, ATy = A @ x, AT @ y
+    traj = [(x, y, Ax, ATy)]
+    for _ in range(K):
+        xn = primal_step(x, ATy, inst.c, inst.lv, inst.uv, tau)
+        Axn = A @ xn
+        yn = dual_step(y, Ax, Axn, inst.lc, inst.uc, sigma)
+        x, y, Ax, ATy = xn, yn, Axn, AT @ yn
+        traj.append((x, y, Ax, ATy))
+    return traj
+
+
+def unrolled_pdhg_vjp(inst, K, eta, omega, gx, gy):
+    """Reverse-mode derivative of (x_K, y_K) = unrolled_pdhg(...)[K] contracted with
+    (gx, gy): the gradients of L = gx'x_K + gy'y_K with respect to c, lc, uc, lv, uv
+    (infinite bounds get 0).  Each step is differentiated piece by piece:
+      x' = clamp(u, lv, uv), u = x - tau (c - A'y): d/du = 1 strictly inside, d/dlv = 1
+        where u < lv, d/duv = 1 where u > uv;
+      y' = yh - clamp(yh, -sigma uc, -sigma lc), yh = y - sigma (2 A x' - A x):
+        d/dyh = 1 where yh < -sigma uc (then d/duc = sigma) or yh > -sigma lc (then
+        d/dlc = sigma), 0 in between;
+    and the start x_0 = clamp(0, lv, uv) likewise.  Returns (x_K, y_K, grads dict)."""
+    A = inst.scipy_csr()
+    AT = A.T.tocsr()
+    tau, sigma = eta / omega, eta * omega
+    traj = unrolled_pdhg(inst, K, eta, omega)
+    g = {k: np.zeros(v) for k, v in (("c", inst.n), ("lc", inst.m), ("uc", inst.m),
+                                     ("lv", inst.n), ("uv", inst.n))}
+    bx, by = np.array(gx, dtype=float), np.array(gy, dtype=float)
+    for k in range(K - 1, -1, -1):
+        x, y, Ax, ATy = traj[k]
+        xn, _, Axn, _ = traj[k + 1]
+        # dual step
+        yh = y - sigma * (2.0 * Axn - Ax)
+        below, above = yh < -sigma * inst.uc, yh > -sigma * inst.lc
+        byh = np.where(below | above, by, 0.0)
+        g["uc"] += np.where(below, sigma * by, 0.0)
+        g["lc"] += np.where(above, sigma * by, 0.0)
+        q = AT @ byh                      # yh = y - sigma A (2x' - x)
+        bxn = bx - 2.0 * sigma * q        # total adjoint of x'
+        by_k = byh.copy()
+        bx_k = sigma * q
+        # primal step
+        u = x - tau * (inst.c - ATy)
+        lo, hi = u < inst.lv, u > inst.uv
+        inside = ~(lo | hi)
+        bu = np.where(inside, bxn, 0.0)
+        g["lv"] += np.where(lo, bxn, 0.0)
+        g["uv"] += np.where(hi, bxn, 0.0)
+        g["c"] += -tau * bu
+        bx_k += bu
+        by_k += tau * (A @ bu)            # u depends on y through A'y
+        bx, by = bx_k, by_k
+    lo0, hi0 = 0.0 < inst.lv, 0.0 > inst.uv    # x_0 = clamp(0, lv, uv); y_0 = 0
+    g["lv"] += np.where(lo0, bx, 0.0)
+    g["uv"] += np.where(hi0, bx, 0.0)
+    for key in ("lc", "uc", "lv", "uv"):
+        g[key] = np.where(np.isfinite(getattr(inst, key)), g[key], 0.0)
+    xK, yK = traj[K][0], traj[K][1]
+    return xK, yK, g

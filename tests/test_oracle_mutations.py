@@ -150,3 +150,30 @@ def test_wrong_slack_cone_is_caught(monkeypatch):
     monkeypatch.setattr(O, "proj_Sbar", bad)
     with pytest.raises(AssertionError):
         PI.test_two_variable_closed_forms()
+
+
+# --- adjoint of unrolled PDHG -------------------------------------------------------
+import inspect  # noqa: E402
+import textwrap  # noqa: E402
+
+from tests import test_oracle_adjoint as PA  # noqa: E402
+
+
+def _mutated_vjp(old, new):
+    src = textwrap.dedent(inspect.getsource(O.unrolled_pdhg_vjp))
+    assert old in src
+    ns = dict(vars(O))
+    exec(src.replace(old, new), ns)  # noqa: S102  (a planted mistake, CPU only)
+    return ns["unrolled_pdhg_vjp"]
+
+
+@pytest.mark.parametrize("old,new", [
+    ("bxn = bx - 2.0 * sigma * q", "bxn = bx - sigma * q"),            # extrapolation factor
+    ("by_k += tau * (A @ bu)", "by_k += 0.0 * (A @ bu)"),             # dropped A'y path
+    ('g["uc"] += np.where(below, sigma * by, 0.0)', 'g["uc"] += np.where(above, sigma * by, 0.0)'),
+    ("inside = ~(lo | hi)", "inside = ~lo"),                          # upper clamp ignored
+])
+def test_adjoint_mistakes_are_caught(monkeypatch, old, new):
+    monkeypatch.setattr(O, "unrolled_pdhg_vjp", _mutated_vjp(old, new))
+    with pytest.raises(AssertionError):
+        PA.test_vjp_matches_central_differences(5)
