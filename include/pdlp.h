@@ -261,6 +261,27 @@ typedef struct {
 int pdlp_solve_batch(int64_t count, const pdlp_problem* problems, const pdlp_params* p,
                      int concurrency, int* status_out, pdlp_stats* stats_out);
 
+/* Unrolled PDHG and its adjoint (a differentiable layer; Eq. (3), Sec. 2): K steps of
+ * Eq. (3) on the LP as given -- no preconditioning, restarts or adaptive steps: the
+ * constant steps are tau = eta/omega, sigma = eta*omega (eta < 1/||A||_2 for the
+ * convergence theory) -- from (proj_X(0), 0), with the dual step
+ * y' = yh - proj_[-sigma uc, -sigma lc](yh), yh = y - sigma (2 A x' - A x).  Writes
+ * x_K (x_out[n]) and y_K (y_out[m]).  With gx[n] and gy[m] non-NULL it also computes the
+ * gradients of L = gx'x_K + gy'y_K with respect to c, lc, uc, lv, uv into the non-NULL
+ * grad_* arrays (the vector-Jacobian product of the unrolled map; at a clamp boundary
+ * the derivative of the inside branch is taken; infinite bounds get 0), by a reverse
+ * pass that recomputes the iterates from checkpoints stored every checkpoint_every
+ * steps (<= 0: 50): memory 2(m+n)(K/checkpoint_every + checkpoint_every + 2) doubles,
+ * time about 3x the forward pass.  FP64.  params: inputs_on_device (host or device
+ * arrays, outputs alike) and cuda_stream are used; the rest is ignored.  Returns 0 or
+ * a negative error code. */
+int pdlp_unrolled_pdhg(int64_t m, int64_t n, const pdlp_csr* A, const double* c,
+                       const double* lc, const double* uc, const double* lv, const double* uv,
+                       int64_t K, double eta, double omega, int64_t checkpoint_every,
+                       const double* gx, const double* gy, const pdlp_params* p, double* x_out,
+                       double* y_out, double* grad_c, double* grad_lc, double* grad_uc,
+                       double* grad_lv, double* grad_uv);
+
 /* Message for the last nonzero return of a call made by this thread. */
 const char* pdlp_last_error(void);
 

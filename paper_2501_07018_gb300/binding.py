@@ -126,6 +126,10 @@ def load_library(path: str | None = None):
     lib.pdlp_kkt_products_noalloc.restype = ctypes.c_int
     lib.pdlp_solve_batch.argtypes = [i64, P, ctypes.POINTER(Params), ctypes.c_int, P, P]
     lib.pdlp_solve_batch.restype = ctypes.c_int
+    lib.pdlp_unrolled_pdhg.argtypes = [i64, i64, ctypes.POINTER(Csr), P, P, P, P, P, i64,
+                                       ctypes.c_double, ctypes.c_double, i64, P, P,
+                                       ctypes.POINTER(Params), P, P, P, P, P, P, P]
+    lib.pdlp_unrolled_pdhg.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -326,6 +330,36 @@ def solve_batch(instances, device: bool = False, concurrency: int = 16, **params
             first_error = ""
         res.append(SolveResult(status[k], x, y, st, []))
     return res
+
+
+GRAD_KEYS = ("c", "lc", "uc", "lv", "uv")
+
+
+def unrolled_pdhg(m, n, row_ptr, col_idx, val, c, lc, uc, lv, uv, K, eta, omega, gx=None,
+                  gy=None, checkpoint_every=50, **params):
+    """pdlp_unrolled_pdhg: (x_K, y_K) of K fixed-step PDHG steps and, when gx, gy are
+    given, the gradients of gx'x_K + gy'y_K with respect to c, lc, uc, lv, uv (dict).
+    Arrays are numpy (host) or torch CUDA tensors (device), outputs alike."""
+    lib = load_library()
+    on_device = _is_cuda_tensor(val) or _is_cuda_tensor(c)
+    mh = _Marshal(on_device)
+    A, vecs = _lp_args(mh, m, n, row_ptr, col_idx, val, c, lc, uc, lv, uv)
+    prm = _params_for(on_device, params)
+    x, xp = mh.out(n)
+    y, yp = mh.out(m)
+    want = gx is not None
+    gptr = [mh(gx, "f64"), mh(gy, "f64")] if want else [None, None]
+    grads, gouts = {}, []
+    for k, ln in zip(GRAD_KEYS, (n, m, m, n, n)):
+        if want:
+            t, p_ = mh.out(ln)
+            grads[k] = t
+            gouts.append(p_)
+        else:
+            gouts.append(None)
+    _check(lib.pdlp_unrolled_pdhg(m, n, ctypes.byref(A), *vecs, int(K), float(eta), float(omega),
+                                  int(checkpoint_every), *gptr, ctypes.byref(prm), xp, yp, *gouts))
+    return x, y, (grads if want else None)
 
 
 def precondition(m, n, row_ptr, col_idx, val, **params):

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "../../include/pdlp.h"
+#include "adjoint.cuh"
 #include "gap.cuh"
 #include "infeas.cuh"
 #include "pdhg.cuh"
@@ -1454,6 +1455,75 @@ int pdlp_solve_batch(int64_t count, const pdlp_problem* problems, const pdlp_par
     work();
     for (auto& t : pool) t.join();
     if (first_index >= 0) set_last_error(first_error);
+    return 0;
+  } catch (...) {
+    return handle_exception();
+  }
+}
+
+int pdlp_unrolled_pdhg(int64_t m, int64_t n, const pdlp_csr* A, const double* c,
+                       const double* lc, const double* uc, const double* lv, const double* uv,
+                       int64_t K, double eta, double omega, int64_t checkpoint_every,
+                       const double* gx, const double* gy, const pdlp_params* p, double* x_out,
+                       double* y_out, double* grad_c, double* grad_lc, double* grad_uc,
+                       double* grad_lv, double* grad_uv) {
+  try {
+    pdlp_params prm;
+    pdlp_params_default(&prm);
+    if (p) prm = *p;
+    const Inputs in = make_inputs(m, n, A, c, lc, uc, lv, uv, &prm);
+    if (K < 0) throw PdlpError(-1, "pdlp_unrolled_pdhg: K < 0");
+    if (!(eta > 0.0) || !std::isfinite(eta) || !(omega > 0.0) || !std::isfinite(omega))
+      throw PdlpError(-1, "pdlp_unrolled_pdhg: eta and omega must be positive and finite");
+    if (!x_out || (m > 0 && !y_out)) throw PdlpError(-1, "pdlp_unrolled_pdhg: null output");
+    if (gx && m > 0 && !gy) throw PdlpError(-1, "pdlp_unrolled_pdhg: gx without gy");
+    StreamGuard sg(prm.cuda_stream);
+    const cudaStream_t s = sg.s;
+    DeviceArena arena;
+    arena.set_stream(s);
+    DevInputs d = stage_inputs(arena, in, s);
+    validate(arena, in, d, s);
+    Problem<double> P;
+    build_problem<double>(arena, in, d, 0, 0.0, P, s);  // identity scaling, renumbered
+    const UnrolledLp L{P.m, P.n, P.A, P.AT, P.c, P.lc, P.uc, P.lv, P.uv, P.perm_r, P.perm_c};
+    const UnrolledProblem U{&L, eta / omega, eta * omega, spmv_grid<double>(P.A, kEpiPlain),
+                            spmv_grid<double>(P.AT, kEpiPlain)};
+    // device views of the caller's arrays
+    auto dev_in = [&](const double* h, int64_t len) -> const double* {
+      if (!h || in.on_device) return h;
+      double* dptr = arena.alloc<double>(len);
+      copy_in(dptr, h, sizeof(double) * len, false, s);
+      return dptr;
+    };
+    auto dev_out = [&](double* h, int64_t len) -> double* {
+      if (!h || in.on_device) return h;
+      return arena.alloc<double>(len);
+    };
+    const double* dgx = dev_in(gx, n);
+    const double* dgy = dev_in(gy, m);
+    double* dx = dev_out(x_out, n);
+    double* dy = dev_out(y_out, m);
+    UnrolledGrads G{dev_out(grad_c, n), dev_out(grad_lc, m), dev_out(grad_uc, m),
+                    dev_out(grad_lv, n), dev_out(grad_uv, n)};
+    if (gx && m == 0) dgy = nullptr;
+    unrolled_pdhg_run(arena, U, K, checkpoint_every > 0 ? checkpoint_every : 50, dgx, dgy, dx,
+                      dy, gx ? &G : nullptr, s);
+    if (!in.on_device) {
+      auto back = [&](double* h, const double* dptr, int64_t len) {
+        if (h && len > 0)
+          PDLP_CUDA_CHECK(cudaMemcpyAsync(h, dptr, sizeof(double) * len, cudaMemcpyDeviceToHost, s));
+      };
+      back(x_out, dx, n);
+      back(y_out, dy, m);
+      if (gx) {
+        back(grad_c, G.c, n);
+        back(grad_lc, G.lc, m);
+        back(grad_uc, G.uc, m);
+        back(grad_lv, G.lv, n);
+        back(grad_uv, G.uv, n);
+      }
+    }
+    PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
     return 0;
   } catch (...) {
     return handle_exception();

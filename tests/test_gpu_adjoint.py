@@ -1,0 +1,131 @@
+"""The adjoint of unrolled PDHG on the CUDA path (pdlp_unrolled_pdhg and the torch
+autograd layer) against the oracle's reverse-mode derivative, against central finite
+differences of the GPU forward map, and against the LP sensitivity closed forms.
+
+Fixed-step PDHG is non-expansive, so the GPU and oracle iterates stay within rounding
+of each other (no amplification as with the adaptive step); gradients are compared at
+1e-9 relative to the largest entry."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import pdlp_oracle as O
+from tests import lp_helpers as H
+from tests import test_oracle_adjoint as PA
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+KEYS = ("c", "lc", "uc", "lv", "uv")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2501_07018_gb300 as p
+
+    return p
+
+
+def _run(pkg, inst, K, eta, omega, gx=None, gy=None, every=50):
+    return pkg.binding.unrolled_pdhg(inst.m, inst.n, inst.row_ptr, inst.col_idx, inst.val, inst.c,
+                                     inst.lc, inst.uc, inst.lv, inst.uv, K, eta, omega, gx=gx,
+                                     gy=gy, checkpoint_every=every)
+
+
+def _close(a, b, rel=1e-9):
+    scale = max(1.0, float(np.max(np.abs(b)))) if b.size else 1.0
+    return float(np.max(np.abs(a - b))) <= rel * scale if b.size else True
+
+
+@pytest.mark.parametrize("seed", [5, 6])
+def test_gradients_match_oracle_for_every_checkpoint_spacing(pkg, seed):
+    for inst in PA._fd_cases(seed):
+        rng = np.random.default_rng(seed)
+        A = inst.scipy_csr().toarray()
+        eta, omega, K = 0.9 / np.linalg.norm(A, 2), 0.8, 150
+        gx, gy = rng.standard_normal(inst.n), rng.standard_normal(inst.m)
+        xo, yo, go = O.unrolled_pdhg_vjp(inst, K, eta, omega, gx, gy)
+        ref = None
+        for every in (1, 7, 50, 1000):
+            x, y, g = _run(pkg, inst, K, eta, omega, gx, gy, every)
+            assert _close(x, xo) and _close(y, yo), inst.name
+            for k in KEYS:
+                assert _close(g[k], go[k]), (inst.name, k, every)
+            if ref is None:
+                ref = (x, y, g)
+            else:  # recomputation from checkpoints is bit-identical
+                assert np.array_equal(x, ref[0]) and np.array_equal(y, ref[1])
+                for k in KEYS:
+                    assert np.array_equal(g[k], ref[2][k]), (k, every)
+
+
+def test_gradients_match_central_differences_of_the_gpu_forward(pkg):
+    import dataclasses
+
+    inst = PA._fd_cases(9)[1]
+    rng = np.random.default_rng(2)
+    A = inst.scipy_csr().toarray()
+    eta, omega, K = 0.9 / np.linalg.norm(A, 2), 1.1, 120
+    gx, gy = rng.standard_normal(inst.n), rng.standard_normal(inst.m)
+    _, _, g = _run(pkg, inst, K, eta, omega, gx, gy, 25)
+
+    def loss(i2):
+        x, y, _ = _run(pkg, i2, K, eta, omega)
+        return float(gx @ x + gy @ y)
+    eq = inst.lc == inst.uc
+    h = 1e-6
+    for key, keys, d in (("c", ("c",), rng.standard_normal(inst.n)),
+                         ("uv", ("uv",), rng.standard_normal(inst.n) * np.isfinite(inst.uv)),
+                         ("lc", ("lc",), rng.standard_normal(inst.m) * (~eq & np.isfinite(inst.lc))),
+                         ("b", ("lc", "uc"), rng.standard_normal(inst.m) * eq)):
+        if not np.any(d):
+            continue
+        plus = dataclasses.replace(inst, **{k: getattr(inst, k) + h * d for k in keys})
+        minus = dataclasses.replace(inst, **{k: getattr(inst, k) - h * d for k in keys})
+        fd = (loss(plus) - loss(minus)) / (2 * h)
+        an = float(sum(g[k] for k in keys) @ d)
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (key, fd, an)
+
+
+def test_sensitivity_closed_forms(pkg):
+    with open(os.path.join(GOLDEN, "textbook_lp.json")) as f:
+        gd = json.load(f)
+    inf = float("inf")
+    conv = lambda v: [inf if s == "inf" else (-inf if s == "-inf" else s) for s in v]  # noqa
+    inst = H.make_lp(gd["A"], gd["c"], conv(gd["lc"]), conv(gd["uc"]), conv(gd["lv"]),
+                     conv(gd["uv"]))
+    A = inst.scipy_csr().toarray()
+    x, y, g = _run(pkg, inst, 3000, 0.9 / np.linalg.norm(A, 2), 1.0, inst.c, np.zeros(inst.m))
+    np.testing.assert_allclose(x + g["c"], gd["x_star"], atol=1e-9)
+    np.testing.assert_allclose(g["uc"], -np.maximum(-np.array(gd["y_star"]), 0.0), atol=1e-9)
+
+
+def test_autograd_layer(pkg):
+    """loss = ||x_K - x_target||^2 through the torch layer: the gradients equal the
+    library's vector-Jacobian product with gx = 2 (x_K - x_target), gy = 0."""
+    import torch
+
+    from paper_2501_07018_gb300.autograd import SparseLp, unrolled_pdhg_layer
+
+    inst = PA._fd_cases(11)[0]
+    A = inst.scipy_csr().toarray()
+    eta = 0.9 / np.linalg.norm(A, 2)
+    dev = lambda a: torch.as_tensor(np.asarray(a)).cuda()  # noqa: E731
+    lp = SparseLp(inst.m, inst.n, dev(inst.row_ptr), dev(inst.col_idx), dev(inst.val))
+    params = [dev(v).clone().requires_grad_(True) for v in (inst.c, inst.lc, inst.uc, inst.lv, inst.uv)]
+    target = torch.linspace(0, 3, inst.n, dtype=torch.float64, device="cuda")
+    x, y = unrolled_pdhg_layer(lp, *params, K=100, eta=eta, omega=1.0, checkpoint_every=10)
+    loss = ((x - target) ** 2).sum()
+    loss.backward()
+    gx = 2.0 * (x.detach() - target)
+    _, _, go = O.unrolled_pdhg_vjp(inst, 100, eta, 1.0, gx.cpu().numpy(), np.zeros(inst.m))
+    for p_, k in zip(params, KEYS):
+        assert _close(p_.grad.cpu().numpy(), go[k]), k
