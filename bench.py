@@ -392,6 +392,7 @@ def run_ours(args):
         del d
         out["polishing_mcf"] = polishing_mcf(pkg)
         out["batch_uneven"] = batch_uneven(pkg)
+        out["adjoint_unrolled"] = adjoint_unrolled(pkg)
         out["cpu_baseline"] = cpu_baseline(args)
     if dist is not None:
         dist.barrier()
@@ -492,6 +493,42 @@ def batch_uneven(pkg, count=128, concurrency=16):
                      "iterations_total": its, "statuses": st,
                      "max_rel_kkt": max(r.stats["rel_kkt"] for r in got)}
     return res
+
+
+def adjoint_unrolled(pkg, count=4, K=2000, every=50):
+    """pdlp_unrolled_pdhg on LPs shaped like the differentiable batch (m=2000, n=5000,
+    8 N(0,1) entries per column): K fixed-step PDHG steps (eta = 0.9/||A||_2), forward
+    alone and forward + reverse pass for loss ||x_K - x_target||^2 with checkpoints every
+    `every` steps; wall clock per LP on device arrays."""
+    import numpy as np
+    import scipy.sparse.linalg as sla
+    import torch
+
+    import lpgen
+    from paper_2501_07018_gb300 import binding
+
+    fw, fb = [], []
+    for k in range(count):
+        inst = lpgen.random_lp(2000, 5000, 8, seed=lpgen.config_seed(3, k))
+        eta = 0.9 / float(sla.svds(inst.scipy_csr(), k=1, return_singular_vectors=False)[0])
+        d = [torch.as_tensor(np.asarray(a)).cuda() for a in
+             (inst.row_ptr, inst.col_idx, inst.val, inst.c, inst.lc, inst.uc, inst.lv, inst.uv)]
+        target = torch.rand(inst.n, dtype=torch.float64, device="cuda") * 10
+        binding.unrolled_pdhg(inst.m, inst.n, *d, 20, eta, 1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, _, _ = binding.unrolled_pdhg(inst.m, inst.n, *d, K, eta, 1.0)
+        torch.cuda.synchronize()
+        fw.append(time.perf_counter() - t0)
+        gy = torch.zeros(inst.m, dtype=torch.float64, device="cuda")
+        t0 = time.perf_counter()
+        binding.unrolled_pdhg(inst.m, inst.n, *d, K, eta, 1.0, gx=2.0 * (x - target), gy=gy,
+                              checkpoint_every=every)
+        torch.cuda.synchronize()
+        fb.append(time.perf_counter() - t0)
+    return {"workload": f"{count} LPs m=2000 n=5000 (8 entries per column), K={K} steps, "
+                        f"checkpoint every {every}",
+            "forward_ms": 1e3 * statistics.median(fw), "forward_backward_ms": 1e3 * statistics.median(fb)}
 
 
 def main():
