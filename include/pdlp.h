@@ -282,6 +282,27 @@ int pdlp_unrolled_pdhg(int64_t m, int64_t n, const pdlp_csr* A, const double* c,
                        double* y_out, double* grad_c, double* grad_lc, double* grad_uc,
                        double* grad_lv, double* grad_uv);
 
+/* One LP of a batch of unrolled-PDHG calls: the arguments of pdlp_unrolled_pdhg. */
+typedef struct {
+  int64_t m, n;
+  pdlp_csr A;
+  const double *c, *lc, *uc, *lv, *uv;
+  int64_t K;
+  double eta, omega;
+  int64_t checkpoint_every;
+  const double *gx, *gy;                      /* NULL: forward only          */
+  double *x_out, *y_out;                      /* [n], [m]                    */
+  double *grad_c, *grad_lc, *grad_uc, *grad_lv, *grad_uv; /* each may be NULL */
+} pdlp_unrolled_problem;
+
+/* pdlp_unrolled_pdhg for `count` LPs, `concurrency` (<= 0: 16) at a time on per-worker
+ * streams and host threads of the calling thread's device (as pdlp_solve_batch).
+ * status_out[count] receives each call's return value.  Returns 0 when every LP was
+ * attempted (pdlp_last_error() then describes the first failed one), or
+ * PDLP_INVALID_ARGUMENT. */
+int pdlp_unrolled_pdhg_batch(int64_t count, const pdlp_unrolled_problem* problems,
+                             const pdlp_params* p, int concurrency, int* status_out);
+
 /* Message for the last nonzero return of a call made by this thread. */
 const char* pdlp_last_error(void);
 

@@ -57,6 +57,18 @@ class Problem(ctypes.Structure):
                 ("x_out", ctypes.c_void_p), ("y_out", ctypes.c_void_p)]
 
 
+class UnrolledProblem(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("A", Csr),
+                ("c", ctypes.c_void_p), ("lc", ctypes.c_void_p), ("uc", ctypes.c_void_p),
+                ("lv", ctypes.c_void_p), ("uv", ctypes.c_void_p), ("K", ctypes.c_int64),
+                ("eta", ctypes.c_double), ("omega", ctypes.c_double),
+                ("checkpoint_every", ctypes.c_int64), ("gx", ctypes.c_void_p),
+                ("gy", ctypes.c_void_p), ("x_out", ctypes.c_void_p), ("y_out", ctypes.c_void_p),
+                ("grad_c", ctypes.c_void_p), ("grad_lc", ctypes.c_void_p),
+                ("grad_uc", ctypes.c_void_p), ("grad_lv", ctypes.c_void_p),
+                ("grad_uv", ctypes.c_void_p)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [
         ("status", ctypes.c_int), ("iterations", ctypes.c_int64), ("attempts", ctypes.c_int64),
@@ -130,6 +142,8 @@ def load_library(path: str | None = None):
                                        ctypes.c_double, ctypes.c_double, i64, P, P,
                                        ctypes.POINTER(Params), P, P, P, P, P, P, P]
     lib.pdlp_unrolled_pdhg.restype = ctypes.c_int
+    lib.pdlp_unrolled_pdhg_batch.argtypes = [i64, P, ctypes.POINTER(Params), ctypes.c_int, P]
+    lib.pdlp_unrolled_pdhg_batch.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -360,6 +374,45 @@ def unrolled_pdhg(m, n, row_ptr, col_idx, val, c, lc, uc, lv, uv, K, eta, omega,
     _check(lib.pdlp_unrolled_pdhg(m, n, ctypes.byref(A), *vecs, int(K), float(eta), float(omega),
                                   int(checkpoint_every), *gptr, ctypes.byref(prm), xp, yp, *gouts))
     return x, y, (grads if want else None)
+
+
+def unrolled_pdhg_batch(items, device: bool = False, concurrency: int = 16, **params) -> list:
+    """pdlp_unrolled_pdhg_batch.  ``items``: dicts with ``lp`` (an object with m, n and
+    the CSR/vector arrays), ``K``, ``eta``, ``omega`` and optionally ``gx``, ``gy``,
+    ``checkpoint_every``.  Returns, per item, (status, x, y, grads or None)."""
+    lib = load_library()
+    mh = _Marshal(device)
+    probs = (UnrolledProblem * max(1, len(items)))()
+    outs = []
+    for k, it in enumerate(items):
+        inst = it["lp"]
+        arrs = [inst.row_ptr, inst.col_idx, inst.val, inst.c, inst.lc, inst.uc, inst.lv, inst.uv]
+        if device:
+            import torch
+
+            arrs = [a if _is_cuda_tensor(a) else torch.as_tensor(np.asarray(a)).cuda() for a in arrs]
+        A, vecs = _lp_args(mh, inst.m, inst.n, *arrs)
+        pr = probs[k]
+        pr.m, pr.n, pr.A = inst.m, inst.n, A
+        pr.c, pr.lc, pr.uc, pr.lv, pr.uv = vecs
+        pr.K, pr.eta, pr.omega = int(it["K"]), float(it["eta"]), float(it.get("omega", 1.0))
+        pr.checkpoint_every = int(it.get("checkpoint_every", 50))
+        x, pr.x_out = mh.out(inst.n)
+        y, pr.y_out = mh.out(inst.m)
+        grads = None
+        if it.get("gx") is not None:
+            pr.gx, pr.gy = mh(it["gx"], "f64"), mh(it["gy"], "f64")
+            grads = {}
+            for key, ln in zip(GRAD_KEYS, (inst.n, inst.m, inst.m, inst.n, inst.n)):
+                t, p_ = mh.out(ln)
+                grads[key] = t
+                setattr(pr, "grad_" + key, p_)
+        outs.append((x, y, grads))
+    prm = _params_for(device, params)
+    status = (ctypes.c_int * max(1, len(items)))()
+    _check(lib.pdlp_unrolled_pdhg_batch(len(items), ctypes.addressof(probs), ctypes.byref(prm),
+                                        int(concurrency), ctypes.addressof(status)))
+    return [(status[k], *outs[k]) for k in range(len(items))]
 
 
 def precondition(m, n, row_ptr, col_idx, val, **params):

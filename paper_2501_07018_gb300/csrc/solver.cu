@@ -1337,6 +1337,59 @@ static Inputs make_inputs(int64_t m, int64_t n, const pdlp_csr* A, const double*
 
 using namespace pdlp;
 
+// Runs call(i, params with a worker stream) for i in [0, count) on `concurrency` host
+// threads of the caller's device, each with its own non-blocking stream; records each
+// return value and the message of the lowest failed index.
+namespace pdlp {
+template <class Call>
+static int run_batch(const char* name, int64_t count, const pdlp_params& prm, int concurrency,
+                     int* status_out, Call call) {
+  int dev = 0;
+  PDLP_CUDA_CHECK(cudaGetDevice(&dev));
+  const int64_t workers =
+      std::max<int64_t>(1, std::min<int64_t>(concurrency <= 0 ? 16 : concurrency, count));
+  std::atomic<int64_t> next{0};
+  std::mutex mu;
+  std::string first_error;
+  int64_t first_index = -1;
+  auto work = [&]() {
+    cudaStream_t s = nullptr;
+    if (cudaSetDevice(dev) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      s = nullptr;
+    }
+    pdlp_params q = prm;
+    q.cuda_stream = s;
+    for (;;) {
+      const int64_t i = next.fetch_add(1);
+      if (i >= count) break;
+      int code;
+      if (!s) {
+        set_last_error(std::string(name) + ": could not create a stream for a worker");
+        code = PDLP_CUDA_ERROR;
+      } else {
+        code = call(i, q);
+      }
+      status_out[i] = code;
+      if (code < 0) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (first_index < 0 || i < first_index) {
+          first_index = i;
+          first_error = std::string("problem ") + std::to_string(i) + ": " + pdlp_last_error();
+        }
+      }
+    }
+    if (s) cudaStreamDestroy(s);
+  };
+  std::vector<std::thread> pool;
+  for (int64_t w = 1; w < workers; ++w) pool.emplace_back(work);
+  work();
+  for (auto& t : pool) t.join();
+  if (first_index >= 0) set_last_error(first_error);
+  return 0;
+}
+}  // namespace pdlp
+
 extern "C" {
 
 void pdlp_params_default(pdlp_params* p) {
@@ -1411,51 +1464,34 @@ int pdlp_solve_batch(int64_t count, const pdlp_problem* problems, const pdlp_par
     prm.trace_out = nullptr;
     prm.polish_log = nullptr;
     prm.polish_log_cap = 0;
-    int dev = 0;
-    PDLP_CUDA_CHECK(cudaGetDevice(&dev));
-    const int64_t workers =
-        std::max<int64_t>(1, std::min<int64_t>(concurrency <= 0 ? 16 : concurrency, count));
-    std::atomic<int64_t> next{0};
-    std::mutex mu;
-    std::string first_error;
-    int64_t first_index = -1;
-    auto work = [&]() {
-      cudaStream_t s = nullptr;
-      if (cudaSetDevice(dev) != cudaSuccess ||
-          cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-        s = nullptr;
-      }
-      pdlp_params q = prm;
-      q.cuda_stream = s;
-      for (;;) {
-        const int64_t i = next.fetch_add(1);
-        if (i >= count) break;
-        const pdlp_problem& pb = problems[i];
-        int code;
-        if (!s) {
-          set_last_error("pdlp_solve_batch: could not create a stream for a worker");
-          code = PDLP_CUDA_ERROR;
-        } else {
-          code = pdlp_solve(pb.m, pb.n, &pb.A, pb.c, pb.lc, pb.uc, pb.lv, pb.uv, &q, pb.x_out,
-                            pb.y_out, stats_out ? &stats_out[i] : nullptr);
-        }
-        status_out[i] = code;
-        if (code < 0) {
-          std::lock_guard<std::mutex> lock(mu);
-          if (first_index < 0 || i < first_index) {
-            first_index = i;
-            first_error = std::string("problem ") + std::to_string(i) + ": " + pdlp_last_error();
-          }
-        }
-      }
-      if (s) cudaStreamDestroy(s);
-    };
-    std::vector<std::thread> pool;
-    for (int64_t w = 1; w < workers; ++w) pool.emplace_back(work);
-    work();
-    for (auto& t : pool) t.join();
-    if (first_index >= 0) set_last_error(first_error);
-    return 0;
+    return pdlp::run_batch("pdlp_solve_batch", count, prm, concurrency, status_out,
+                     [&](int64_t i, const pdlp_params& q) {
+                       const pdlp_problem& pb = problems[i];
+                       return pdlp_solve(pb.m, pb.n, &pb.A, pb.c, pb.lc, pb.uc, pb.lv, pb.uv, &q,
+                                         pb.x_out, pb.y_out, stats_out ? &stats_out[i] : nullptr);
+                     });
+  } catch (...) {
+    return handle_exception();
+  }
+}
+
+int pdlp_unrolled_pdhg_batch(int64_t count, const pdlp_unrolled_problem* problems,
+                             const pdlp_params* p, int concurrency, int* status_out) {
+  try {
+    if (count < 0) throw PdlpError(-1, "pdlp_unrolled_pdhg_batch: count < 0");
+    if (count > 0 && (!problems || !status_out))
+      throw PdlpError(-1, "pdlp_unrolled_pdhg_batch: null problems or status_out");
+    pdlp_params prm;
+    pdlp_params_default(&prm);
+    if (p) prm = *p;
+    return pdlp::run_batch("pdlp_unrolled_pdhg_batch", count, prm, concurrency, status_out,
+                     [&](int64_t i, const pdlp_params& q) {
+                       const pdlp_unrolled_problem& u = problems[i];
+                       return pdlp_unrolled_pdhg(u.m, u.n, &u.A, u.c, u.lc, u.uc, u.lv, u.uv, u.K,
+                                                 u.eta, u.omega, u.checkpoint_every, u.gx, u.gy,
+                                                 &q, u.x_out, u.y_out, u.grad_c, u.grad_lc,
+                                                 u.grad_uc, u.grad_lv, u.grad_uv);
+                     });
   } catch (...) {
     return handle_exception();
   }

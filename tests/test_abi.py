@@ -50,6 +50,7 @@ def test_struct_layout_matches_header(lib):
         "pdlp_stats": [f for f, _ in binding.Stats._fields_],
         "pdlp_csr": [f for f, _ in binding.Csr._fields_],
         "pdlp_problem": [f for f, _ in binding.Problem._fields_],
+        "pdlp_unrolled_problem": [f for f, _ in binding.UnrolledProblem._fields_],
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
     for st, fs in fields.items():
@@ -68,7 +69,8 @@ def test_struct_layout_matches_header(lib):
         st, f, v = line.split()
         got[(st, f)] = int(v)
     for st, cls in (("pdlp_params", binding.Params), ("pdlp_stats", binding.Stats),
-                    ("pdlp_csr", binding.Csr), ("pdlp_problem", binding.Problem)):
+                    ("pdlp_csr", binding.Csr), ("pdlp_problem", binding.Problem),
+                    ("pdlp_unrolled_problem", binding.UnrolledProblem)):
         assert got[(st, "size")] == ctypes.sizeof(cls), st
         for f, _ in cls._fields_:
             assert got[(st, f)] == getattr(cls, f).offset, (st, f)

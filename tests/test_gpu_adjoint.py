@@ -129,3 +129,27 @@ def test_autograd_layer(pkg):
     _, _, go = O.unrolled_pdhg_vjp(inst, 100, eta, 1.0, gx.cpu().numpy(), np.zeros(inst.m))
     for p_, k in zip(params, KEYS):
         assert _close(p_.grad.cpu().numpy(), go[k]), k
+
+
+def test_batch_equals_single_calls(pkg):
+    """pdlp_unrolled_pdhg_batch: every LP's outputs and gradients equal, bit for bit, a
+    single call on it (forward-only items included)."""
+    items, singles = [], []
+    for seed in (5, 6, 7):
+        for inst in PA._fd_cases(seed):
+            rng = np.random.default_rng(seed)
+            eta = 0.9 / np.linalg.norm(inst.scipy_csr().toarray(), 2)
+            gx, gy = rng.standard_normal(inst.n), rng.standard_normal(inst.m)
+            items.append(dict(lp=inst, K=80, eta=eta, omega=0.9, gx=gx, gy=gy, checkpoint_every=9))
+            singles.append(_run(pkg, inst, 80, eta, 0.9, gx, gy, 9))
+    items.append(dict(lp=items[0]["lp"], K=80, eta=items[0]["eta"], omega=0.9))
+    singles.append(_run(pkg, items[0]["lp"], 80, items[0]["eta"], 0.9))
+    got = pkg.binding.unrolled_pdhg_batch(items, concurrency=4)
+    for (st, x, y, g), (xs, ys, gs) in zip(got, singles):
+        assert st == 0
+        assert np.array_equal(x, xs) and np.array_equal(y, ys)
+        if gs is None:
+            assert g is None
+        else:
+            for k in KEYS:
+                assert np.array_equal(g[k], gs[k]), k
