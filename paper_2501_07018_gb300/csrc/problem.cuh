@@ -105,17 +105,18 @@ void transpose_csr(DeviceArena& arena, const int64_t* row_ptr, const int32_t* co
                    const double* val, int64_t m, int64_t n, int64_t nnz, int64_t* t_row_ptr,
                    int32_t* t_col, double* t_val, cudaStream_t s);
 
-// kind: 0 = max |a| over the row, 1 = sum |a|, 2 = (sum |a|^p)^(1/p)
-void row_norms(const int64_t* row_ptr, const double* val, int64_t rows, int kind, double p,
-               double* out, cudaStream_t s);
+// kind: 0 = max |a| over the row, 1 = sum |a|, 2 = (sum |a|^p)^(1/p); nnz = row_ptr[rows]
+// (sets the lanes per row).
+void row_norms(const int64_t* row_ptr, const double* val, int64_t rows, int64_t nnz, int kind,
+               double p, double* out, cudaStream_t s);
 // out_i = (v_i > 0) ? 1/sqrt(v_i) : 1 ;  acc_i *= out_i
 void scale_factors(const double* norms, int64_t len, double* factors, double* acc,
                    cudaStream_t s);
 // val_e <- (val_e * f_col[col_e]) * f_row[row]   when col_first (A-side: f_col = row
 // factor of A applied first ...).  See setup.cu for the exact operand order.
 void scale_values(const int64_t* row_ptr, const int32_t* col, double* val, int64_t rows,
-                  const double* f_first, const double* f_second, bool first_is_col,
-                  cudaStream_t s);
+                  int64_t nnz, const double* f_first, const double* f_second,
+                  bool first_is_col, cudaStream_t s);
 double max_abs(DeviceArena& arena, const double* v, int64_t len, cudaStream_t s);
 
 // Permutation sorting `count` rows by decreasing length (ties by index): perm[new] = old,

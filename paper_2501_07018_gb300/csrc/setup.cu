@@ -443,7 +443,36 @@ void gather_f64(const double* in, const int32_t* perm, double* out, int64_t len,
 // preconditioning passes
 // ---------------------------------------------------------------------------
 // One group of G lanes per row (G chosen from the mean row length); the loop trip
-// count is uniform across a warp so the group shuffles are safe.
+// count is uniform across a warp so the group shuffles are safe.  The max norm (kind 0)
+// runs on the integer pipe: for the finite non-negative |a_ij| the IEEE bit patterns
+// order as the values do, so the max of the patterns with the sign bit cleared is the
+// pattern of the max, exactly.  On GB300 a double fmax per lane (one per entry and one
+// per step of the group's shuffle tree) made the FP64 pipe the bound of this pass.
+template <int G>
+__global__ void k_row_max(const int64_t* rp, const double* val, int64_t rows, double* out) {
+  const int lane = threadIdx.x & 31, lg = lane % G;
+  const int64_t per_warp = 32 / G;
+  const int64_t warp = gtid() >> 5, nwarps = gstride() >> 5;
+  const unsigned long long* bits = reinterpret_cast<const unsigned long long*>(val);
+  constexpr unsigned long long kMag = 0x7fffffffffffffffULL;
+  for (int64_t i0 = warp * per_warp; i0 < rows; i0 += nwarps * per_warp) {
+    const int64_t i = i0 + lane / G;
+    unsigned long long acc = 0;
+    if (i < rows)
+      for (int64_t e = rp[i] + lg; e < rp[i + 1]; e += G) {
+        const unsigned long long a = bits[e] & kMag;
+        acc = a > acc ? a : acc;
+      }
+#pragma unroll
+    for (int o = G >> 1; o > 0; o >>= 1) {
+      const unsigned long long t = __shfl_xor_sync(0xffffffffu, acc, o, G);
+      acc = t > acc ? t : acc;
+    }
+    if (i < rows && lg == 0) out[i] = __longlong_as_double((long long)acc);
+  }
+}
+
+// Sums |a| (kind 1) or |a|^p (kind 2) per row, p-th root for kind 2.
 template <int G>
 __global__ void k_row_norms(const int64_t* rp, const double* val, int64_t rows, int kind,
                             double p, double* out) {
@@ -456,19 +485,11 @@ __global__ void k_row_norms(const int64_t* rp, const double* val, int64_t rows, 
     if (i < rows) {
       for (int64_t e = rp[i] + lg; e < rp[i + 1]; e += G) {
         const double a = fabs(val[e]);
-        if (kind == 0)
-          acc = fmax(acc, a);
-        else if (kind == 1)
-          acc += a;
-        else
-          acc += pow(a, p);
+        acc += kind == 1 ? a : pow(a, p);
       }
     }
 #pragma unroll
-    for (int o = G >> 1; o > 0; o >>= 1) {
-      const double t = __shfl_xor_sync(0xffffffffu, acc, o, G);
-      acc = (kind == 0) ? fmax(acc, t) : acc + t;
-    }
+    for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
     if (i < rows && lg == 0) out[i] = (kind == 2 && acc > 0.0) ? pow(acc, 1.0 / p) : acc;
   }
 }
@@ -540,17 +561,20 @@ __global__ void k_max_abs_partial(const double* v, int64_t len, double* part) {
     default: CALL(32); break;           \
   }
 
-void row_norms(const int64_t* rp, const double* val, int64_t rows, int kind, double p,
-               double* out, cudaStream_t s) {
+void row_norms(const int64_t* rp, const double* val, int64_t rows, int64_t nnz, int kind,
+               double p, double* out, cudaStream_t s) {
   if (rows == 0) return;
-  int64_t nnz = 0;
-  PDLP_CUDA_CHECK(cudaMemcpyAsync(&nnz, rp + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
   const int g = group_for(nnz, rows);
   const unsigned grid = grid_for((rows * g + 31) / 32 * 32);
+#define PDLP_MAX(G) k_row_max<G><<<grid, kThreads, 0, s>>>(rp, val, rows, out)
 #define PDLP_NORMS(G) k_row_norms<G><<<grid, kThreads, 0, s>>>(rp, val, rows, kind, p, out)
-  PDLP_GROUP_DISPATCH(g, PDLP_NORMS)
+  if (kind == 0) {
+    PDLP_GROUP_DISPATCH(g, PDLP_MAX)
+  } else {
+    PDLP_GROUP_DISPATCH(g, PDLP_NORMS)
+  }
 #undef PDLP_NORMS
+#undef PDLP_MAX
   PDLP_LAUNCH_CHECK();
 }
 void scale_factors(const double* norms, int64_t len, double* f, double* acc, cudaStream_t s) {
@@ -559,12 +583,9 @@ void scale_factors(const double* norms, int64_t len, double* f, double* acc, cud
   PDLP_LAUNCH_CHECK();
 }
 void scale_values(const int64_t* rp, const int32_t* col, double* val, int64_t rows,
-                  const double* f_first, const double* f_second, bool first_is_col,
-                  cudaStream_t s) {
+                  int64_t nnz, const double* f_first, const double* f_second,
+                  bool first_is_col, cudaStream_t s) {
   if (rows == 0) return;
-  int64_t nnz = 0;
-  PDLP_CUDA_CHECK(cudaMemcpyAsync(&nnz, rp + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
   const int g = group_for(nnz, rows);
   const unsigned grid = grid_for((rows * g + 31) / 32 * 32);
 #define PDLP_SCALE(G) \

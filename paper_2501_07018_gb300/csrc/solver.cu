@@ -334,12 +334,12 @@ static void build_problem(DeviceArena& arena, const Inputs& in, const DevInputs&
   k_fill<<<vec_grid(n), kThreads, 0, s>>>(P.d2, n, 1.0);
   PDLP_LAUNCH_CHECK();
   auto pass = [&](int kind_r, double p_r, int kind_c, double p_c) {
-    row_norms(P.A.row_ptr, P.val64, m, kind_r, p_r, nr, s);
-    row_norms(P.AT.row_ptr, P.valT64, n, kind_c, p_c, nc, s);
+    row_norms(P.A.row_ptr, P.val64, m, nnz, kind_r, p_r, nr, s);
+    row_norms(P.AT.row_ptr, P.valT64, n, nnz, kind_c, p_c, nc, s);
     scale_factors(nr, m, fr, P.d1, s);
     scale_factors(nc, n, fs, P.d2, s);
-    scale_values(P.A.row_ptr, P.A.col, P.val64, m, fr, fs, false, s);
-    scale_values(P.AT.row_ptr, P.AT.col, P.valT64, n, fr, fs, true, s);
+    scale_values(P.A.row_ptr, P.A.col, P.val64, m, nnz, fr, fs, false, s);
+    scale_values(P.AT.row_ptr, P.AT.col, P.valT64, n, nnz, fr, fs, true, s);
     P.launches += 6;
   };
   for (int it = 0; it < ruiz_iters; ++it) pass(0, 0.0, 0, 0.0);
