@@ -473,7 +473,7 @@ def polishing_mcf(pkg, scale=0.01, plain_limit_s=30.0):
     d = [torch.as_tensor(np.asarray(a)).cuda() for a in
          (inst.row_ptr, inst.col_idx, inst.val, inst.c, inst.lc, inst.uc, inst.lv, inst.uv)]
     crit = dict(termination_mode=1, eps_abs_feas=1e-8, eps_rel_gap=1e-2, max_iters=10**7)
-    res = {"workload": inst.name + f" (m={inst.m} n={inst.n} nnz={inst.nnz}), 1/100 of the "
+    res = {"workload": inst.name + f" (m={inst.m} n={inst.n} nnz={inst.nnz}), {scale:g} of the "
                                    "one-GPU multicommodity-flow size"}
     for name, extra in (("fp32_bulk_polished", dict(precision=pkg.FP32_BULK, feasibility_polishing=1,
                                                     time_limit_s=120.0)),
@@ -495,9 +495,8 @@ def polishing_mcf(pkg, scale=0.01, plain_limit_s=30.0):
 
 def batch_uneven(pkg, count=128, concurrency=16):
     """pdlp_solve_batch on ``count`` LPs of the uneven-size batch (m ~ U{500..20000},
-    n ~ U{1.5m..3m}, 4-12 entries per column), FP32 bulk with FP64 checks, each to
-    relative KKT 1e-6: wall clock with host arrays, LPs/s and the iterations of all LPs
-    per second."""
+    n ~ U{1.5m..3m}, 4-12 entries per column), FP64, each to relative KKT 1e-6: wall
+    clock with host arrays, LPs/s and the iterations of all LPs per second."""
     import lpgen
 
     insts = lpgen.config2(count)

@@ -166,6 +166,8 @@ typedef struct {
   int64_t polish_pauses;   /* Algorithm 4: pauses of normal PDLP                     */
   int64_t polish_primal_iters, polish_dual_iters; /* iterations of all phases      */
   int64_t polish_accepted_k; /* k of the pause whose pair was returned, else 0     */
+  int64_t device_bytes;    /* device memory the call allocated (stream-ordered; all of
+                              it is held until the call returns, so this is its peak) */
 } pdlp_stats;
 
 /* Fills *p with the defaults listed above. */

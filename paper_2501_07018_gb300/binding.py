@@ -91,6 +91,7 @@ class Stats(ctypes.Structure):
         ("gap_failures", ctypes.c_int64),
         ("polish_pauses", ctypes.c_int64), ("polish_primal_iters", ctypes.c_int64),
         ("polish_dual_iters", ctypes.c_int64), ("polish_accepted_k", ctypes.c_int64),
+        ("device_bytes", ctypes.c_int64),
     ]
 
     def as_dict(self):

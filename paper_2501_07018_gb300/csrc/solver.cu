@@ -1270,6 +1270,7 @@ struct Solver {
       st->polish_primal_iters = pol.primal_iters + (aux64 ? aux64->pol.primal_iters : 0);
       st->polish_dual_iters = pol.dual_iters + (aux64 ? aux64->pol.dual_iters : 0);
       st->polish_accepted_k = pol.accepted_k;
+      st->device_bytes = (int64_t)(arena.total() + (aux64 ? aux64->arena.total() : 0));
     }
     return status;
   }
