@@ -95,6 +95,8 @@ def test_solve_objective_at_rel_kkt_1e8(pkg, name):
     assert abs(own["pobj"] - res.stats["pobj"]) <= 1e-9 * abs(own["pobj"])
     assert np.all(res.x >= inst.lv) and np.all(res.x <= inst.uv)
     assert res.stats["gap_failures"] == 0, res.stats.get("gap_failure_message")
+    # the call's device memory: at least the staged CSR (12 B per entry) and the vectors
+    assert res.stats["device_bytes"] >= 12 * inst.nnz + 8 * 5 * (inst.m + inst.n)
 
 
 def test_host_and_device_inputs_identical(pkg):
