@@ -75,6 +75,10 @@ used):
       R1's start, with the dual step of R17/R18; at a clamp boundary (u = lv, yh =
       -sigma uc, ...) the derivative of the inside branch is taken as 0 for the
       iterate (measure-zero set).
+
+Parity unpinned: the sequence of restart decisions of ``PdlpRun`` (criteria (i)-(iii)
+under R4-R8) has no pin outside this module; everything else is pinned by the tests
+(closed forms, brute force, HiGHS, finite differences, hand-solved LPs).
 """
 from __future__ import annotations
 
