@@ -135,29 +135,98 @@ void unrolled_forward_step(const UnrolledProblem& U, const State& s, const State
   launch_spmv_plain<double>(U.P->AT, t.y, t.aty, U.grid_at, st);
 }
 
+// A launch sequence captured once from a stream and replayed as a CUDA graph.  capture()
+// returns false (nothing launched, no error left pending) where the stream cannot be
+// captured; the caller then launches the sequence directly.
+class Replay {
+ public:
+  Replay() = default;
+  Replay(const Replay&) = delete;
+  Replay& operator=(const Replay&) = delete;
+  ~Replay() {
+    if (exec_) cudaGraphExecDestroy(exec_);
+  }
+  template <class F>
+  bool capture(cudaStream_t st, F&& body) {
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return false;
+    }
+    cudaGraph_t g = nullptr;
+    try {
+      body();
+    } catch (...) {
+      cudaStreamEndCapture(st, &g);
+      if (g) cudaGraphDestroy(g);
+      (void)cudaGetLastError();
+      throw;
+    }
+    const cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (e != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      (void)cudaGetLastError();
+      return false;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&exec_, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      exec_ = nullptr;
+      (void)cudaGetLastError();
+      return false;
+    }
+    return true;
+  }
+  void launch(cudaStream_t st) { PDLP_CUDA_CHECK(cudaGraphLaunch(exec_, st)); }
+
+ private:
+  cudaGraphExec_t exec_ = nullptr;
+};
+
 int64_t unrolled_pdhg_run(DeviceArena& arena, const UnrolledProblem& U, int64_t K,
                           int64_t every, const double* gx, const double* gy, double* x_out,
                           double* y_out, UnrolledGrads* grads, cudaStream_t st) {
   const int64_t m = U.P->m, n = U.P->n;
   const int64_t C = std::max<int64_t>(1, every);
   const int64_t ncp = K / C + 1;  // checkpoints at k = 0, C, 2C, ...
+  const int64_t full = K / C;     // segments of C steps that end at a checkpoint
+  const size_t state_bytes = sizeof(double) * 2 * (size_t)(m + n);
   double* cp = arena.alloc<double>(ncp * 2 * (m + n));
   double* seg = arena.alloc<double>((C + 1) * 2 * (m + n));
   int64_t launches = 0;
-  // forward: checkpoints, the last state in seg
-  State s0 = state_at(cp, 0, m, n);
+  auto copy_state = [&](const State& dst, const State& src) {
+    PDLP_CUDA_CHECK(cudaMemcpyAsync(dst.x, src.x, state_bytes, cudaMemcpyDeviceToDevice, st));
+  };
+  // forward: the running state alternates between seg slots 0 and 1, every full segment
+  // starting in slot 0 (one captured sequence of C steps, replayed), its last state
+  // copied to the checkpoint
+  const State s0 = state_at(cp, 0, m, n);
   k_ad_start<<<vgrid(std::max(m, n)), kThreads, 0, st>>>(U.P->lv, U.P->uv, s0.x, s0.y, s0.aty, m, n);
   PDLP_LAUNCH_CHECK();
   launch_spmv_plain<double>(U.P->A, s0.x, s0.ax, U.grid_a, st);
   launches += 2;
-  State cur = s0;
-  for (int64_t k = 0; k < K; ++k) {
-    const int64_t kn = k + 1;
-    const State nxt = (kn % C == 0) ? state_at(cp, kn / C, m, n) : state_at(seg, kn % 2, m, n);
-    unrolled_forward_step(U, cur, nxt, st);
-    launches += 4;
-    cur = nxt;
+  copy_state(state_at(seg, 0, m, n), s0);
+  auto forward_steps = [&](int64_t count) {
+    for (int64_t i = 0; i < count; ++i)
+      unrolled_forward_step(U, state_at(seg, i % 2, m, n), state_at(seg, (i + 1) % 2, m, n), st);
+  };
+  {
+    Replay fwd;
+    const bool graph = full >= 2 && fwd.capture(st, [&] { forward_steps(C); });
+    for (int64_t sg = 0; sg < full; ++sg) {
+      if (graph)
+        fwd.launch(st);
+      else
+        forward_steps(C);
+      launches += 4 * C;
+      const State end = state_at(seg, C % 2, m, n);
+      copy_state(state_at(cp, sg + 1, m, n), end);
+      if (C % 2) copy_state(state_at(seg, 0, m, n), end);
+    }
   }
+  const int64_t rest = K - full * C;
+  forward_steps(rest);
+  launches += 4 * rest;
+  const State cur = state_at(seg, rest % 2, m, n);
   // outputs x_K, y_K in the caller's numbering
   k_scatter<<<vgrid(n), kThreads, 0, st>>>(cur.x, U.P->perm_c, x_out, n);
   if (m) k_scatter<<<vgrid(m), kThreads, 0, st>>>(cur.y, U.P->perm_r, y_out, m);
@@ -181,19 +250,13 @@ int64_t unrolled_pdhg_run(DeviceArena& arena, const UnrolledProblem& U, int64_t 
   gather_f64(gx, U.P->perm_c, bx, n, st);
   if (m) gather_f64(gy, U.P->perm_r, by, m, st);
   launches += 2;
-  for (int64_t sgi = (K - 1) / C; K > 0 && sgi >= 0; --sgi) {
-    const int64_t k0 = sgi * C, k1 = std::min(K, k0 + C);
-    // recompute states k0 .. k1 into seg[0 .. k1-k0]
-    const State a = state_at(cp, sgi, m, n);
-    State t0 = state_at(seg, 0, m, n);
-    PDLP_CUDA_CHECK(cudaMemcpyAsync(t0.x, a.x, sizeof(double) * 2 * (m + n),
-                                    cudaMemcpyDeviceToDevice, st));
-    for (int64_t k = k0; k < k1; ++k) {
-      unrolled_forward_step(U, state_at(seg, k - k0, m, n), state_at(seg, k - k0 + 1, m, n), st);
-      launches += 4;
-    }
-    for (int64_t k = k1 - 1; k >= k0; --k) {
-      const State s = state_at(seg, k - k0, m, n), t = state_at(seg, k - k0 + 1, m, n);
+  // one segment from its checkpoint (already in seg slot 0): recompute its states into
+  // seg[0 .. steps], then the reverse steps from the last to the first
+  auto segment_back = [&](int64_t steps) {
+    for (int64_t i = 0; i < steps; ++i)
+      unrolled_forward_step(U, state_at(seg, i, m, n), state_at(seg, i + 1, m, n), st);
+    for (int64_t i = steps - 1; i >= 0; --i) {
+      const State s = state_at(seg, i, m, n), t = state_at(seg, i + 1, m, n);
       if (m) {
         k_ad_back_rows<<<vgrid(m), kThreads, 0, st>>>(s.y, s.ax, t.ax, U.P->lc, U.P->uc, U.sigma,
                                                       by, byh, g[1], g[2], m);
@@ -208,7 +271,19 @@ int64_t unrolled_pdhg_run(DeviceArena& arena, const UnrolledProblem& U, int64_t 
         k_ad_back_y<<<vgrid(m), kThreads, 0, st>>>(byh, r, U.tau, by, m);
         PDLP_LAUNCH_CHECK();
       }
-      launches += 5;
+    }
+  };
+  {
+    Replay bwd;
+    const bool graph = full >= 2 && bwd.capture(st, [&] { segment_back(C); });
+    for (int64_t sgi = (K - 1) / C; K > 0 && sgi >= 0; --sgi) {
+      const int64_t k0 = sgi * C, steps = std::min(K, k0 + C) - k0;
+      copy_state(state_at(seg, 0, m, n), state_at(cp, sgi, m, n));
+      if (graph && steps == C)
+        bwd.launch(st);
+      else
+        segment_back(steps);
+      launches += 9 * steps;
     }
   }
   k_ad_finish<<<vgrid(std::max(m, n)), kThreads, 0, st>>>(bx, U.P->lc, U.P->uc, U.P->lv, U.P->uv,
