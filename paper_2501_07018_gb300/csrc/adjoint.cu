@@ -22,6 +22,7 @@
 
 #include "../../include/pdlp.h"
 #include "adjoint.cuh"
+#include "graph.cuh"
 
 namespace pdlp {
 namespace {
@@ -134,53 +135,6 @@ void unrolled_forward_step(const UnrolledProblem& U, const State& s, const State
   }
   launch_spmv_plain<double>(U.P->AT, t.y, t.aty, U.grid_at, st);
 }
-
-// A launch sequence captured once from a stream and replayed as a CUDA graph.  capture()
-// returns false (nothing launched, no error left pending) where the stream cannot be
-// captured; the caller then launches the sequence directly.
-class Replay {
- public:
-  Replay() = default;
-  Replay(const Replay&) = delete;
-  Replay& operator=(const Replay&) = delete;
-  ~Replay() {
-    if (exec_) cudaGraphExecDestroy(exec_);
-  }
-  template <class F>
-  bool capture(cudaStream_t st, F&& body) {
-    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-      (void)cudaGetLastError();
-      return false;
-    }
-    cudaGraph_t g = nullptr;
-    try {
-      body();
-    } catch (...) {
-      cudaStreamEndCapture(st, &g);
-      if (g) cudaGraphDestroy(g);
-      (void)cudaGetLastError();
-      throw;
-    }
-    const cudaError_t e = cudaStreamEndCapture(st, &g);
-    if (e != cudaSuccess || !g) {
-      if (g) cudaGraphDestroy(g);
-      (void)cudaGetLastError();
-      return false;
-    }
-    const cudaError_t ei = cudaGraphInstantiate(&exec_, g, 0);
-    cudaGraphDestroy(g);
-    if (ei != cudaSuccess) {
-      exec_ = nullptr;
-      (void)cudaGetLastError();
-      return false;
-    }
-    return true;
-  }
-  void launch(cudaStream_t st) { PDLP_CUDA_CHECK(cudaGraphLaunch(exec_, st)); }
-
- private:
-  cudaGraphExec_t exec_ = nullptr;
-};
 
 int64_t unrolled_pdhg_run(DeviceArena& arena, const UnrolledProblem& U, int64_t K,
                           int64_t every, const double* gx, const double* gy, double* x_out,

@@ -23,6 +23,7 @@
 #include "../../include/pdlp.h"
 #include "adjoint.cuh"
 #include "gap.cuh"
+#include "graph.cuh"
 #include "infeas.cuh"
 #include "pdhg.cuh"
 
@@ -783,6 +784,54 @@ struct Solver {
     launches += 3;
   }
 
+  // Step attempts replayed from captured graphs (chunks of 64, 32, ..., 1 attempts) when
+  // per-kernel timing is off: the three launches of an attempt take the same arguments
+  // throughout a run (the device state picks the buffers and decides acceptance), so a
+  // graph is keyed by the run's buffers, the step-factor table and the chunk length.
+  struct SlotGraph {
+    IterBuffers<T> b;
+    DevState* dst;
+    const double* tab;
+    int64_t len, count;
+    std::unique_ptr<Replay> replay;
+  };
+  std::vector<SlotGraph> slot_graphs;
+  bool slot_graphs_ok = true;
+
+  Replay* slot_graph(Run<T>& r, int64_t count) {
+    for (auto& g : slot_graphs)
+      if (g.count == count && g.dst == r.dst && g.tab == step_tab && g.len == step_len &&
+          std::memcmp(&g.b, &r.b, sizeof(r.b)) == 0)
+        return g.replay.get();
+    std::unique_ptr<Replay> rp(new Replay);
+    const int64_t saved = launches;  // captured launches run when the graph is replayed
+    const bool ok = rp->capture(s, [&] {
+      for (int64_t q = 0; q < count; ++q) launch_slot(r);
+    });
+    launches = saved;
+    if (!ok) {
+      slot_graphs_ok = false;
+      return nullptr;
+    }
+    slot_graphs.push_back(SlotGraph{r.b, r.dst, step_tab, step_len, count, std::move(rp)});
+    return slot_graphs.back().replay.get();
+  }
+
+  void launch_slots(Run<T>& r, int64_t count) {
+    while (count > 0) {
+      int64_t c = 64;
+      while (c > count) c >>= 1;
+      Replay* g = (!timer.on && slot_graphs_ok) ? slot_graph(r, c) : nullptr;
+      if (!g) {
+        for (int64_t q = 0; q < count; ++q) launch_slot(r);
+        return;
+      }
+      g->launch(s);
+      launches += 3 * c;
+      count -= c;
+    }
+  }
+
   // first n (>= 1) such that restart condition (iii) t+j >= beta (k+j) holds
   int64_t steps_to_artificial(int64_t k, int64_t t) const {
     const double be = prm.beta_art;
@@ -874,7 +923,7 @@ struct Solver {
       bool error = false;
       while (r.k < target) {
         const int64_t need = (trace_iters > r.k) ? 1 : (target - r.k);
-        for (int64_t q = 0; q < need; ++q) launch_slot(r);
+        launch_slots(r, need);
         const double omega_used = r.hs.omega;
         pull_state(r);
         if (r.hs.error) {
