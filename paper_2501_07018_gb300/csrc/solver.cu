@@ -42,6 +42,12 @@ void set_last_error_cstr(const char* msg, const char* detail) {
     std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
 }
 
+// Set on the worker threads of a batch: their solves launch step attempts directly.
+// With many LPs in flight the GPU, not the launching thread, sets the pace, and each
+// graph instantiation (taken under a driver-wide lock) is pure cost: the 128-LP batch
+// took 17.6 s with per-LP graphs against 13.9 s with direct launches.
+static thread_local bool t_batch_worker = false;
+
 __device__ __forceinline__ int64_t sgi() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ int64_t sgs() { return (int64_t)gridDim.x * blockDim.x; }
 
@@ -582,7 +588,9 @@ struct Solver {
   T *Xk = nullptr, *Yk = nullptr;                          // (x^k, y^k) of the pause
   T *Xt = nullptr, *AXt = nullptr, *Yt = nullptr, *ATYt = nullptr;  // polished pair
 
-  Solver(const pdlp_params& p, cudaStream_t st) : prm(p), s(st) { arena.set_stream(st); }
+  Solver(const pdlp_params& p, cudaStream_t st) : prm(p), s(st), slot_graphs_ok(!t_batch_worker) {
+    arena.set_stream(st);
+  }
 
   void alloc_shared() {
     const int64_t m = P.m, n = P.n;
@@ -784,52 +792,50 @@ struct Solver {
     launches += 3;
   }
 
-  // Step attempts replayed from captured graphs (chunks of 64, 32, ..., 1 attempts) when
-  // per-kernel timing is off: the three launches of an attempt take the same arguments
+  // Step attempts replayed from captured graphs of 64 attempts (the span between two
+  // checks; shorter spans launch directly) when per-kernel timing is off and the call is
+  // not part of a batch: the three launches of an attempt take the same arguments
   // throughout a run (the device state picks the buffers and decides acceptance), so a
-  // graph is keyed by the run's buffers, the step-factor table and the chunk length.
+  // graph is keyed by the run's buffers and the step-factor table.
+  static constexpr int64_t kSlotChunk = 64;
   struct SlotGraph {
     IterBuffers<T> b;
     DevState* dst;
     const double* tab;
-    int64_t len, count;
+    int64_t len;
     std::unique_ptr<Replay> replay;
   };
   std::vector<SlotGraph> slot_graphs;
-  bool slot_graphs_ok = true;
+  bool slot_graphs_ok;
 
-  Replay* slot_graph(Run<T>& r, int64_t count) {
+  Replay* slot_graph(Run<T>& r) {
     for (auto& g : slot_graphs)
-      if (g.count == count && g.dst == r.dst && g.tab == step_tab && g.len == step_len &&
+      if (g.dst == r.dst && g.tab == step_tab && g.len == step_len &&
           std::memcmp(&g.b, &r.b, sizeof(r.b)) == 0)
         return g.replay.get();
     std::unique_ptr<Replay> rp(new Replay);
     const int64_t saved = launches;  // captured launches run when the graph is replayed
     const bool ok = rp->capture(s, [&] {
-      for (int64_t q = 0; q < count; ++q) launch_slot(r);
+      for (int64_t q = 0; q < kSlotChunk; ++q) launch_slot(r);
     });
     launches = saved;
     if (!ok) {
       slot_graphs_ok = false;
       return nullptr;
     }
-    slot_graphs.push_back(SlotGraph{r.b, r.dst, step_tab, step_len, count, std::move(rp)});
+    slot_graphs.push_back(SlotGraph{r.b, r.dst, step_tab, step_len, std::move(rp)});
     return slot_graphs.back().replay.get();
   }
 
   void launch_slots(Run<T>& r, int64_t count) {
-    while (count > 0) {
-      int64_t c = 64;
-      while (c > count) c >>= 1;
-      Replay* g = (!timer.on && slot_graphs_ok) ? slot_graph(r, c) : nullptr;
-      if (!g) {
-        for (int64_t q = 0; q < count; ++q) launch_slot(r);
-        return;
-      }
+    while (count >= kSlotChunk && !timer.on && slot_graphs_ok) {
+      Replay* g = slot_graph(r);
+      if (!g) break;
       g->launch(s);
-      launches += 3 * c;
-      count -= c;
+      launches += 3 * kSlotChunk;
+      count -= kSlotChunk;
     }
+    for (int64_t q = 0; q < count; ++q) launch_slot(r);
   }
 
   // first n (>= 1) such that restart condition (iii) t+j >= beta (k+j) holds
@@ -1403,6 +1409,8 @@ static int run_batch(const char* name, int64_t count, const pdlp_params& prm, in
   std::string first_error;
   int64_t first_index = -1;
   auto work = [&]() {
+    const bool was_worker = t_batch_worker;
+    t_batch_worker = true;
     cudaStream_t s = nullptr;
     if (cudaSetDevice(dev) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1430,6 +1438,7 @@ static int run_batch(const char* name, int64_t count, const pdlp_params& prm, in
       }
     }
     if (s) cudaStreamDestroy(s);
+    t_batch_worker = was_worker;
   };
   std::vector<std::thread> pool;
   for (int64_t w = 1; w < workers; ++w) pool.emplace_back(work);
