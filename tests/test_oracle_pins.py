@@ -442,7 +442,7 @@ def test_pock_chambolle_alpha1_row_col_l1():
     lp = O.precondition(inst, ruiz_iters=0, pc_alpha=1.0)
     r = np.abs(Ad).sum(1)
     c = np.abs(Ad).sum(0)
-    d1 = np.where(r > 0, 1 / np.sqrt(r), 1.0)
+    d1 = 1 / np.sqrt(np.where(r > 0, r, 1.0))  # a zero row keeps factor 1
     d2 = 1 / np.sqrt(c)
     np.testing.assert_allclose(lp.d1, d1, rtol=1e-15)
     np.testing.assert_allclose(lp.d2, d2, rtol=1e-15)
