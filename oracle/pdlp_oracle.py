@@ -76,9 +76,10 @@ used):
       -sigma uc, ...) the derivative of the inside branch is taken as 0 for the
       iterate (measure-zero set).
 
-Parity unpinned: the sequence of restart decisions of ``PdlpRun`` (criteria (i)-(iii)
-under R4-R8) has no pin outside this module; everything else is pinned by the tests
-(closed forms, brute force, HiGHS, finite differences, hand-solved LPs).
+Parity unpinned: the restart decisions of ``PdlpRun`` by criteria (i) and (ii) (under
+R4-R8) have no pin outside this module; criterion (iii) alone is pinned by its
+closed-form schedule, and everything else by the tests (closed forms, brute force,
+HiGHS, finite differences, hand-solved LPs).
 """
 from __future__ import annotations
 

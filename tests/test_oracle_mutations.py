@@ -177,3 +177,23 @@ def test_adjoint_mistakes_are_caught(monkeypatch, old, new):
     monkeypatch.setattr(O, "unrolled_pdhg_vjp", _mutated_vjp(old, new))
     with pytest.raises(AssertionError):
         PA.test_vjp_matches_central_differences(5)
+
+
+# --- restart bookkeeping --------------------------------------------------------------
+def _mutated_run(old, new):
+    src = textwrap.dedent(inspect.getsource(O.PdlpRun.run))
+    assert src.count(old) == 1
+    ns = dict(vars(O))
+    exec(src.replace(old, new), ns)  # noqa: S102  (a planted mistake, CPU only)
+    return ns["run"]
+
+
+@pytest.mark.parametrize("old,new", [
+    ("self.t = 0\n", "self.t = self.t\n"),                            # t kept across a restart
+    ("(t >= prm.beta_art * k)", "(t > prm.beta_art * k)"),            # strict criterion (iii)
+    ("self.k += 1", "self.k += 1 + (self.t == 1)"),                   # k counts an extra step
+])
+def test_restart_bookkeeping_mistakes_are_caught(monkeypatch, old, new):
+    monkeypatch.setattr(O.PdlpRun, "run", _mutated_run(old, new))
+    with pytest.raises(AssertionError):
+        P.test_artificial_restarts_follow_the_closed_form_schedule(0.5, 2, 1)

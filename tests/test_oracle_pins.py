@@ -450,6 +450,27 @@ def test_pock_chambolle_alpha1_row_col_l1():
     assert lp.lv[0] == 0 and lp.uv[0] == pytest.approx(1 / d2[0], rel=1e-15)
 
 
+@pytest.mark.parametrize("beta_art,num,den", [(0.5, 2, 1), (0.25, 4, 3)])
+def test_artificial_restarts_follow_the_closed_form_schedule(beta_art, num, den):
+    """Restart criterion (iii) of Sec. 3 alone (beta_suff = beta_nec = 0 switch (i) and
+    (ii) off away from an exact optimum; no termination): a restart at k_j resets t, so
+    the next one falls at the first k with k - k_j >= beta_art k, i.e.
+    k_{j+1} = ceil(k_j / (1 - beta_art)) = ceil(num k_j / den), from k_1 = 1 -- powers of
+    two for beta_art = 1/2.  Pins the counting of k and t (R3, R4) and the reset."""
+    iters = 300
+    prm = O.Params(beta_suff=0.0, beta_nec=0.0, beta_art=beta_art, eps_rel_kkt=0.0,
+                   max_iters=iters, detect_infeasibility=False)
+    res = O.solve(lpgen.config0(), prm, trace_iters=iters)
+    got = [(r["k"], r["restart"]) for r in res.trace if r["restart"] != O.RESTART_NONE]
+    want, k = [], 1
+    while k < iters:
+        want.append(k)
+        k = -(-num * k // den)
+    assert [k for k, _ in got] == want
+    assert all(kind == O.RESTART_ARTIFICIAL for _, kind in got)
+    assert res.stats["restarts"] == [0, 0, len(want)]
+
+
 def test_primal_weight_closed_form():
     """Algorithm 3 with theta = 1/2 is the geometric mean of omega and Dy/Dx; outside
     (eps0, 1/eps0) the weight is kept."""
