@@ -76,10 +76,11 @@ used):
       -sigma uc, ...) the derivative of the inside branch is taken as 0 for the
       iterate (measure-zero set).
 
-Parity unpinned: the restart decisions of ``PdlpRun`` by criteria (i) and (ii) (under
-R4-R8) have no pin outside this module; criterion (iii) alone is pinned by its
-closed-form schedule, and everything else by the tests (closed forms, brute force,
-HiGHS, finite differences, hand-solved LPs).
+Parity unpinned: the restart decisions of ``PdlpRun`` by criterion (ii), and by (i) at
+its paper threshold, have no pin outside this module (they turn on gap values only the
+method produces); the schedules of (iii) alone and of an always-true (i) are pinned in
+closed form, and everything else by the tests (closed forms, brute force, HiGHS, finite
+differences, hand-solved LPs).
 """
 from __future__ import annotations
 

@@ -197,3 +197,14 @@ def test_restart_bookkeeping_mistakes_are_caught(monkeypatch, old, new):
     monkeypatch.setattr(O.PdlpRun, "run", _mutated_run(old, new))
     with pytest.raises(AssertionError):
         P.test_artificial_restarts_follow_the_closed_form_schedule(0.5, 2, 1)
+
+
+@pytest.mark.parametrize("old,new", [
+    ("if prm.restarts and is_check and self.mu_ref is not None:",
+     "if prm.restarts and self.mu_ref is not None:"),                # (i) between checks
+    ("if kind == RESTART_NONE and is_art:", "if is_art:"),            # (iii) overrides (i)
+])
+def test_restart_criterion_order_mistakes_are_caught(monkeypatch, old, new):
+    monkeypatch.setattr(O.PdlpRun, "run", _mutated_run(old, new))
+    with pytest.raises(AssertionError):
+        P.test_sufficient_decay_restarts_only_at_checks()

@@ -471,6 +471,21 @@ def test_artificial_restarts_follow_the_closed_form_schedule(beta_art, num, den)
     assert res.stats["restarts"] == [0, 0, len(want)]
 
 
+def test_sufficient_decay_restarts_only_at_checks():
+    """Criterion (i) of Sec. 3 with beta_suff so large that it always holds: it is only
+    evaluated at the periodic checks (every 64 iterations, R4), after the first restart
+    has set mu(z^{n,0}, z^{n-1,0}) (R5), and it takes precedence over (iii) when both
+    apply.  So (iii) restarts at k = 1, 2, 4, ..., 32 and (i) at every multiple of 64."""
+    iters = 300
+    prm = O.Params(beta_suff=1e300, beta_nec=0.0, eps_rel_kkt=0.0, max_iters=iters,
+                   detect_infeasibility=False)
+    res = O.solve(lpgen.config0(), prm, trace_iters=iters)
+    got = [(r["k"], r["restart"]) for r in res.trace if r["restart"] != O.RESTART_NONE]
+    want = [(2 ** j, O.RESTART_ARTIFICIAL) for j in range(6)]
+    want += [(k, O.RESTART_SUFFICIENT) for k in range(64, iters, 64)]
+    assert got == want
+
+
 def test_primal_weight_closed_form():
     """Algorithm 3 with theta = 1/2 is the geometric mean of omega and Dy/Dx; outside
     (eps0, 1/eps0) the weight is kept."""
