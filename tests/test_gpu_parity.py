@@ -47,6 +47,29 @@ def _trace_parity(pkg, inst, iters=100, **prm):
     return res, ora, errs
 
 
+def test_restart_schedules_in_closed_form(pkg):
+    """The closed-form restart schedules the oracle is pinned to: (iii) alone restarts at
+    k_{j+1} = ceil(k_j / (1 - beta_art)); an always-true (i) fires exactly at the checks
+    and before (iii).  Exercises the host's look-ahead to the next (iii) iteration."""
+    inst = lpgen.config0()
+    iters = 300
+    cases = []
+    for beta_art, num, den in ((0.5, 2, 1), (0.25, 4, 3)):
+        want, k = [], 1
+        while k < iters:
+            want.append((k, O.RESTART_ARTIFICIAL))
+            k = -(-num * k // den)
+        cases.append((dict(beta_suff=0.0, beta_nec=0.0, beta_art=beta_art), want))
+    want = [(2 ** j, O.RESTART_ARTIFICIAL) for j in range(6)]
+    want += [(k, O.RESTART_SUFFICIENT) for k in range(64, iters, 64)]
+    cases.append((dict(beta_suff=1e300, beta_nec=0.0), want))
+    for prm, want in cases:
+        res = pkg.solve_instance(inst, trace_iters=iters, max_iters=iters, eps_rel_kkt=0.0,
+                                 detect_infeasibility=0, **prm)
+        got = [(r["k"], r["restart"]) for r in res.trace if r["restart"] != 0]
+        assert got == want, prm
+
+
 @pytest.mark.parametrize("name", ["config0", "edge", "edge_long", "powerlaw", "mcf"])
 def test_trace_parity_first_100_iterations(pkg, name):
     """Iterates, accepted steps and restart decisions of the first 100 iterations.
