@@ -24,6 +24,7 @@
 #include "adjoint.cuh"
 #include "gap.cuh"
 #include "graph.cuh"
+#include "host_logic.h"
 #include "infeas.cuh"
 #include "pdhg.cuh"
 
@@ -840,17 +841,7 @@ struct Solver {
 
   // first n (>= 1) such that restart condition (iii) t+j >= beta (k+j) holds
   int64_t steps_to_artificial(int64_t k, int64_t t) const {
-    const double be = prm.beta_art;
-    int64_t j = 1;
-    if (be < 1.0) {
-      const double need = (be * (double)k - (double)t) / (1.0 - be);
-      if (need > 1.0) j = (int64_t)std::ceil(need);
-      while (j > 1 && (double)(t + j - 1) >= be * (double)(k + j - 1)) --j;
-      while (!((double)(t + j) >= be * (double)(k + j))) ++j;
-    } else {
-      j = std::numeric_limits<int64_t>::max() / 4;
-    }
-    return j;
+    return pdlp::steps_to_artificial(k, t, prm.beta_art);
   }
 
   // Starts run r on the LP with scaled vectors (c, lc, uc, lv, uv) from (x_start,
@@ -990,14 +981,8 @@ struct Solver {
           return kRunTime;
         }
       }
-      int kind = 0;
-      if (is_check && r.have_mu_ref) {
-        if (mu_c <= prm.beta_suff * r.mu_ref)
-          kind = 1;
-        else if (mu_c <= prm.beta_nec * r.mu_ref && mu_c > r.mu_c_prev)
-          kind = 2;
-      }
-      if (kind == 0 && is_art) kind = 3;
+      const int kind = restart_kind(is_check, is_art, r.have_mu_ref, mu_c, r.mu_ref,
+                                    r.mu_c_prev, prm.beta_suff, prm.beta_nec);
       if (is_check) r.mu_c_prev = mu_c;
       if (kind == 0) continue;
       // restart the outer loop at the candidate
@@ -1018,9 +1003,7 @@ struct Solver {
       PDLP_CUDA_CHECK(cudaMemcpyAsync(d2h, dist_out, sizeof(d2h), cudaMemcpyDeviceToHost, s));
       PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
       const double dx = std::sqrt(d2h[0]), dy = std::sqrt(d2h[1]);
-      double om = r.hs.omega;
-      if (prm.eps_zero < dx && dx < 1.0 / prm.eps_zero && prm.eps_zero < dy && dy < 1.0 / prm.eps_zero)
-        om = std::exp(prm.theta * std::log(dy / dx) + (1.0 - prm.theta) * std::log(om));
+      const double om = primal_weight(r.hs.omega, dx, dy, prm.theta, prm.eps_zero);
       r.mu_ref = gap(r, current(r), om);
       r.have_mu_ref = true;
       k_copy2<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(r.b.X[cur], r.X0, n, r.b.Y[cur], r.Y0, m);
