@@ -124,6 +124,13 @@ typedef struct {
                               when it is positive and x_i - lv_i <= |x_i|, or
                               negative and uv_i - x_i <= |x_i|, else 0 (robust to
                               huge bounds; changes the measures, not the iterates) */
+  double fixed_step;       /* > 0: every step attempt uses eta = fixed_step and is
+                              accepted (plain PDHG of Eq. (3) with constant steps, the
+                              Chambolle-Pock iteration Algorithm 2 adapts); 0
+                              (default): Algorithm 2.  Must be finite and >= 0.   */
+  double fixed_omega;      /* > 0: the primal weight is fixed_omega throughout (no
+                              InitializePrimalWeight, no Algorithm 3 update at
+                              restarts); 0 (default): Sec. 3's rules.  Finite, >= 0. */
 } pdlp_params;
 
 /* Row of params->polish_log for one pause of Algorithm 4:

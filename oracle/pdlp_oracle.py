@@ -76,11 +76,12 @@ used):
       -sigma uc, ...) the derivative of the inside branch is taken as 0 for the
       iterate (measure-zero set).
 
-Parity unpinned: the restart decisions of ``PdlpRun`` by criterion (ii), and by (i) at
-its paper threshold, have no pin outside this module (they turn on gap values only the
-method produces); the schedules of (iii) alone and of an always-true (i) are pinned in
-closed form, and everything else by the tests (closed forms, brute force, HiGHS, finite
-differences, hand-solved LPs).
+Pins (tests/): closed forms, brute force, HiGHS, finite differences and hand-solved LPs
+for every function.  The restart decisions of ``PdlpRun`` are pinned by closed-form
+schedules: (iii) alone; an always-true (i); and (i) and (ii) at the paper's thresholds
+on fixed-step PDHG for a 1 x 1 equality-constrained LP with a free variable, where the
+iteration is a 2 x 2 linear map and the normalized gap is the omega-dual norm of the
+gradient, plus a nilpotent instance on which (ii) must wait for a strict rise.
 """
 from __future__ import annotations
 

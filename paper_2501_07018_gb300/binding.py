@@ -47,6 +47,7 @@ class Params(ctypes.Structure):
         ("polish_log", ctypes.c_void_p),
         ("detect_infeasibility", ctypes.c_int), ("eps_infeas", ctypes.c_double),
         ("reduced_costs", ctypes.c_int),
+        ("fixed_step", ctypes.c_double), ("fixed_omega", ctypes.c_double),
     ]
 
 

@@ -185,6 +185,7 @@ struct DevState {
   double last_dx2, last_dy2, last_inter, last_eta_bar;
   int32_t max_retries;
   int32_t pad_;
+  double fixed_eta;   // > 0: constant step, every attempt accepted (no Algorithm 2)
 };
 
 struct Counters {

@@ -12,12 +12,16 @@ namespace pdlp {
 
 // The first j >= 1 for which restart criterion (iii), t + j >= beta_art (k + j), holds
 // after j more accepted iterations from (k accepted in total, t since the last restart);
-// a quarter of INT64_MAX ("never") when beta_art >= 1.  The host synchronises with the
-// device at that iteration at the latest.
+// a quarter of INT64_MAX ("never") when beta_art >= 1 or is NaN, and also when that j
+// exceeds 2^52 (no run gets that far; beyond it the doubles of the test below no
+// longer resolve single iterations).  The host synchronises with the device at that
+// iteration at the latest.
 inline int64_t steps_to_artificial(int64_t k, int64_t t, double beta_art) {
-  if (!(beta_art < 1.0)) return std::numeric_limits<int64_t>::max() / 4;
+  const int64_t never = std::numeric_limits<int64_t>::max() / 4;
+  if (!(beta_art < 1.0)) return never;
   int64_t j = 1;
   const double need = (beta_art * (double)k - (double)t) / (1.0 - beta_art);
+  if (!(need < 4503599627370496.0)) return never;  // 2^52, NaN included
   if (need > 1.0) j = (int64_t)std::ceil(need);
   // the estimate may be off by rounding: settle on the first j that satisfies the test
   while (j > 1 && (double)(t + j - 1) >= beta_art * (double)(k + j - 1)) --j;

@@ -460,16 +460,17 @@ __global__ void __launch_bounds__(kSpmvThreads, PDLP_SPMV_MINB(T)) k_spmv(SpmvAr
     red_f = 1.0 - pow(kf, -0.3);
     grow_f = 1.0 + pow(kf, -0.6);
   }
-  const double eta_new = fmin(red_f * eta_bar, grow_f * eta);
+  const double eta_new = s->fixed_eta > 0.0 ? s->fixed_eta : fmin(red_f * eta_bar, grow_f * eta);
   s->attempts += 1;
   s->last_dx2 = dx2;
   s->last_dy2 = dy2;
   s->last_inter = inter;
   s->last_eta_bar = eta_bar;
+  const bool fixed = s->fixed_eta > 0.0;  // constant-step PDHG: accept as is
   if (!(isfinite(eta_new) && isfinite(num))) {
     s->error = 1;
     s->accepted = 0;
-  } else if (eta <= eta_bar) {
+  } else if (fixed || eta <= eta_bar) {
     s->eta_acc = eta;
     s->eta_hat = eta_new;
     s->eta = eta_new;

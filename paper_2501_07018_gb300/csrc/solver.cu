@@ -877,6 +877,7 @@ struct Solver {
     r.hs.eta_hat = eta_hat;
     r.hs.omega = omega;
     r.hs.max_retries = prm.max_step_retries;
+    r.hs.fixed_eta = prm.fixed_step > 0.0 ? prm.fixed_step : 0.0;
     push_state(r);
     r.goal = goal;
     r.max_iters = max_iters;
@@ -1003,7 +1004,8 @@ struct Solver {
       PDLP_CUDA_CHECK(cudaMemcpyAsync(d2h, dist_out, sizeof(d2h), cudaMemcpyDeviceToHost, s));
       PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
       const double dx = std::sqrt(d2h[0]), dy = std::sqrt(d2h[1]);
-      const double om = primal_weight(r.hs.omega, dx, dy, prm.theta, prm.eps_zero);
+      const double om = prm.fixed_omega > 0.0 ? prm.fixed_omega
+                                              : primal_weight(r.hs.omega, dx, dy, prm.theta, prm.eps_zero);
       r.mu_ref = gap(r, current(r), om);
       r.have_mu_ref = true;
       k_copy2<T><<<vec_grid(std::max(m, n)), kThreads, 0, s>>>(r.b.X[cur], r.X0, n, r.b.Y[cur], r.Y0, m);
@@ -1217,8 +1219,10 @@ struct Solver {
     if (prm.detect_infeasibility) alloc_infeas();
     const int64_t m = P.m, n = P.n;
 
-    const double eta0 = P.max_abs > 0.0 ? 1.0 / P.max_abs : 1.0;
-    const double omega0 = (P.c_norm_s > 0.0 && P.b_norm_s > 0.0) ? P.c_norm_s / P.b_norm_s : 1.0;
+    double eta0 = P.max_abs > 0.0 ? 1.0 / P.max_abs : 1.0;
+    double omega0 = (P.c_norm_s > 0.0 && P.b_norm_s > 0.0) ? P.c_norm_s / P.b_norm_s : 1.0;
+    if (prm.fixed_step > 0.0) eta0 = prm.fixed_step;
+    if (prm.fixed_omega > 0.0) omega0 = prm.fixed_omega;
     // z^{0,0} = (proj_X(0), 0)
     start_run(main_run, nullptr, nullptr, omega0, eta0, prm.max_iters, kGoalOptimal, P.c, P.lc,
               P.uc, P.lv, P.uv);
@@ -1465,6 +1469,8 @@ void pdlp_params_default(pdlp_params* p) {
   p->reduced_costs = 0;
   p->polish_log_cap = 0;
   p->polish_log = nullptr;
+  p->fixed_step = 0.0;
+  p->fixed_omega = 0.0;
 }
 
 const char* pdlp_last_error(void) { return g_last_error; }
@@ -1481,6 +1487,11 @@ int pdlp_solve(int64_t m, int64_t n, const pdlp_csr* A, const double* c, const d
     if (prm.pc_alpha >= 2.0) throw PdlpError(-1, "pc_alpha must be < 2");
     if (prm.max_iters < 1 || prm.check_period < 1 || prm.max_step_retries < 1)
       throw PdlpError(-1, "max_iters, check_period and max_step_retries must be >= 1");
+    if (!(prm.beta_art >= 0.0) || std::isnan(prm.beta_suff) || std::isnan(prm.beta_nec))
+      throw PdlpError(-1, "beta_art must be >= 0 (>= 1: criterion (iii) off); beta_suff and beta_nec not NaN");
+    if (!(prm.fixed_step >= 0.0 && std::isfinite(prm.fixed_step)) ||
+        !(prm.fixed_omega >= 0.0 && std::isfinite(prm.fixed_omega)))
+      throw PdlpError(-1, "fixed_step and fixed_omega must be finite and >= 0");
     StreamGuard sg(prm.cuda_stream);
     if (prm.precision == PDLP_FP32_BULK) {
       Solver<float> S(prm, sg.s);

@@ -70,6 +70,48 @@ def test_restart_schedules_in_closed_form(pkg):
         assert got == want, prm
 
 
+@pytest.mark.parametrize("case", ["paper_thresholds", "decay_bound", "strict_increase"])
+def test_restart_criteria_i_ii_in_closed_form(pkg, case):
+    """The closed-form schedules that pin criteria (i) and (ii) in the oracle (fixed-step
+    PDHG on 1 x 1 equality-constrained LPs with a free variable, no preconditioning):
+    (i) and (ii) at the paper's thresholds, (ii) held back by its decay bound, and (ii)
+    needing a strict rise of the candidate gap.  The device's normalized gap must also
+    equal the closed form mu = |a| ||(u, v)|| at every evaluation."""
+    from tests import test_oracle_pins as P
+
+    if case == "paper_thresholds":
+        inst, iters, want = P.bilinear_instance(), 200, P.BILINEAR_SCHEDULE
+        prm = dict(fixed_step=0.25, fixed_omega=4.0, check_period=10)
+        cf = (1.0, 1.0, -1.0, 0.25, 4.0, 10, iters, 0.1, 0.9, 0.5)
+    elif case == "decay_bound":
+        inst, iters, want = P.bilinear_instance(), 200, P.SECOND_BILINEAR_SCHEDULE
+        prm = dict(fixed_step=11 / 32, fixed_omega=4.0, check_period=3)
+        cf = (1.0, 1.0, -1.0, 11 / 32, 4.0, 3, iters, 0.1, 0.9, 0.5)
+    else:
+        inst, iters, want = P.nilpotent_instance(), 40, P.NILPOTENT_SCHEDULE
+        prm = dict(fixed_step=1.0, fixed_omega=1.0, check_period=3, beta_suff=-1.0, beta_art=0.9)
+        cf = (1.0, 2.0, 1.0, 1.0, 1.0, 3, iters, -1.0, 0.9, 0.9)
+    _, ev = P._bilinear_1x1_schedule(*cf)
+    res = pkg.solve_instance(inst, trace_iters=iters, max_iters=iters, eps_rel_kkt=-1.0,
+                             ruiz_iters=0, pc_alpha=0.0, detect_infeasibility=0, **prm)
+    got = [(r["k"], r["restart"]) for r in res.trace if r["restart"] != 0]
+    assert got == want
+    for r in res.trace:
+        if r["k"] in ev:
+            _, _, _, mc, ma = ev[r["k"]]
+            assert r["mu_cur"] == pytest.approx(mc, rel=1e-10, abs=1e-300), r["k"]
+            assert r["mu_avg"] == pytest.approx(ma, rel=1e-10, abs=1e-300), r["k"]
+
+
+def test_fixed_step_and_weight_rejected_when_invalid(pkg):
+    inst = lpgen.config0()
+    for bad in (dict(fixed_step=-1.0), dict(fixed_omega=math.inf), dict(beta_art=math.nan),
+                dict(beta_art=-0.5)):
+        with pytest.raises(pkg.PdlpError) as ei:
+            pkg.solve_instance(inst, max_iters=10, **bad)
+        assert ei.value.code == -1, bad
+
+
 @pytest.mark.parametrize("name", ["config0", "edge", "edge_long", "powerlaw", "mcf"])
 def test_trace_parity_first_100_iterations(pkg, name):
     """Iterates, accepted steps and restart decisions of the first 100 iterations.

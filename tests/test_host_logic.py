@@ -97,6 +97,21 @@ def test_lookahead_at_large_counts(run):
         assert j == 1 or not (float(t + j - 1) >= b * float(k + j - 1))
 
 
+def test_lookahead_beyond_range_is_never(run):
+    """beta_art just below 1 at large k: the next (iii) iteration lies beyond 2^52 steps
+    (here ~1e19), where a double no longer resolves single iterations; the look-ahead
+    answers "never" at once instead of converting that count to an integer or stepping
+    towards it; NaN likewise."""
+    b = 1.0 - 2.0**-53
+    cases = [(1000, 0, b), (10**6, 3, b), (2**40, 1, 1.0 - 2.0**-40), (5, 1, math.nan)]
+    got = run([f"S {k} {t} {float(bb).hex()}" for k, t, bb in cases])
+    assert [int(g) for g in got] == [NEVER] * len(cases)
+    # just inside the range the exact answer is still returned
+    k, t, bb = 2**20, 0, 1.0 - 2.0**-30
+    j = int(run([f"S {k} {t} {float(bb).hex()}"])[0])
+    assert float(t + j) >= bb * float(k + j) and not (float(t + j - 1) >= bb * float(k + j - 1))
+
+
 def _kind(is_check, is_art, have, mu_c, mu_ref, mu_prev, bs, bn):
     # Sec. 3: (i) sufficient decay, (ii) necessary decay without progress -- both at the
     # periodic evaluations once the reference gap exists -- else (iii) artificial

@@ -208,3 +208,43 @@ def test_restart_criterion_order_mistakes_are_caught(monkeypatch, old, new):
     monkeypatch.setattr(O.PdlpRun, "run", _mutated_run(old, new))
     with pytest.raises(AssertionError):
         P.test_sufficient_decay_restarts_only_at_checks()
+
+
+def _mutated_run_multi(pairs):
+    src = textwrap.dedent(inspect.getsource(O.PdlpRun.run))
+    for old, new in pairs:
+        assert src.count(old) == 1, old
+        src = src.replace(old, new)
+    ns = dict(vars(O))
+    exec(src, ns)  # noqa: S102  (a planted mistake, CPU only)
+    return ns["run"]
+
+
+@pytest.mark.parametrize("pairs,pin", [
+    # (ii) taken with a non-strict rise of the candidate gap
+    ([("mu_c > self.mu_c_prev", "mu_c >= self.mu_c_prev")],
+     P.test_necessary_decay_needs_a_strict_increase),
+    # the previous candidate gap kept across a restart
+    ([("self.mu_c_prev = math.inf\n", "pass\n")],
+     P.test_restart_criteria_i_and_ii_at_the_paper_thresholds),
+    # (ii) evaluated at (iii) iterations between the checks, (i) still only at checks
+    ([("if prm.restarts and is_check and self.mu_ref is not None:",
+       "if prm.restarts and self.mu_ref is not None:"),
+      ("if mu_c <= prm.beta_suff * self.mu_ref:", "if is_check and mu_c <= prm.beta_suff * self.mu_ref:")],
+     P.test_restart_criteria_i_and_ii_at_the_paper_thresholds),
+    # beta_suff and beta_nec swapped
+    ([("prm.beta_suff * self.mu_ref", "@SWAP@"), ("prm.beta_nec * self.mu_ref", "prm.beta_suff * self.mu_ref"),
+      ("@SWAP@", "prm.beta_nec * self.mu_ref")],
+     P.test_restart_criteria_i_and_ii_at_the_paper_thresholds),
+    # (ii) without the decay bound
+    ([("elif mu_c <= prm.beta_nec * self.mu_ref and mu_c > self.mu_c_prev:",
+       "elif mu_c > self.mu_c_prev:")],
+     P.test_necessary_decay_needs_the_decay_bound),
+    # the candidate chosen the other way round on a tie or in general
+    ([("if mu_cur < mu_avg:", "if mu_cur <= mu_avg and False:")],
+     P.test_restart_criteria_i_and_ii_at_the_paper_thresholds),
+])
+def test_restart_criteria_ii_mistakes_are_caught(monkeypatch, pairs, pin):
+    monkeypatch.setattr(O.PdlpRun, "run", _mutated_run_multi(pairs))
+    with pytest.raises(AssertionError):
+        pin()

@@ -486,6 +486,164 @@ def test_sufficient_decay_restarts_only_at_checks():
     assert got == want
 
 
+def _bilinear_1x1_schedule(a, b, c, eta, omega, period, iters, beta_suff, beta_nec, beta_art):
+    """Restart schedule of fixed-step PDHG on  min c x  s.t.  a x = b  (x free, one
+    equality row, no preconditioning), from closed forms written here, not the
+    oracle's code.
+
+    Iterates: in the coordinates u = sqrt(omega) (x - x*), v = (y - y*) / sqrt(omega)
+    around the saddle point (x*, y*) = (b/a, c/a), one step of Eq. (3) with tau =
+    eta/omega, sigma = eta omega is the linear map  u' = u + h v,
+    v' = -h u + (1 - 2 h^2) v,  h = eta a.
+    Normalized gap: with every bound infinite, L(x, yh) - L(xh, y) is linear in
+    (xh - x, yh - y) with gradient (a y - c, -(a x - b)); its maximum over the ball of
+    omega-radius r is r times the dual norm of that gradient, so
+    mu(z, z_ref) = |a| sqrt(u^2 + v^2) for any z_ref != z, whatever the radius.
+    The average since a restart is the plain mean (equal weights eta).
+    Rules of Sec. 3: at the periodic checks (k a multiple of ``period``) once
+    mu(z^{n,0}, z^{n-1,0}) exists, (i) mu_c <= beta_suff mu_ref, else (ii) mu_c <=
+    beta_nec mu_ref with mu_c above the previous check's candidate gap in the same
+    outer loop; else (iii) t >= beta_art k.  Returns the restarts [(k, kind)] and
+    the candidate gap, mu_ref and kind at every evaluation {k: (mu_c, mu_ref, kind)}."""
+    M = np.array([[1.0, eta * a], [-eta * a, 1.0 - 2.0 * (eta * a) ** 2]])
+    w = np.array([math.sqrt(omega) * (0.0 - b / a), (0.0 - c / a) / math.sqrt(omega)])
+    mu = lambda v: abs(a) * float(np.hypot(v[0], v[1]))  # noqa: E731
+    k = t = 0
+    mu_ref, mu_prev, acc = None, math.inf, np.zeros(2)
+    out, ev = [], {}
+    for _ in range(iters):
+        w = M @ w
+        acc = acc + w
+        k, t = k + 1, t + 1
+        check, art = k % period == 0, t >= beta_art * k
+        if not (check or art):
+            continue
+        avg = acc / t
+        cand = w if mu(w) < mu(avg) else avg
+        mu_c = mu(cand)
+        kind = 0
+        if check and mu_ref is not None:
+            if mu_c <= beta_suff * mu_ref:
+                kind = 1
+            elif mu_c <= beta_nec * mu_ref and mu_c > mu_prev:
+                kind = 2
+        if kind == 0 and art:
+            kind = 3
+        ev[k] = (mu_c, mu_ref, kind, mu(w), mu(avg))
+        if check:
+            mu_prev = mu_c
+        if kind:
+            out.append((k, kind))
+            w, mu_ref, mu_prev, acc, t = cand.copy(), mu(cand), math.inf, np.zeros(2), 0
+    return out, ev
+
+
+# min -x s.t. x = 1: x* = 1, y* = -1; eta = 1/4, omega = 4 (tau = 1/16, sigma = 1: exact)
+BILINEAR_SCHEDULE = [(1, 3), (2, 3), (4, 3), (8, 3), (16, 3), (32, 3), (64, 3), (90, 1),
+                     (130, 2), (180, 1)]
+
+
+def bilinear_instance():
+    return H.make_lp(np.array([[1.0]]), np.array([-1.0]), np.array([1.0]), np.array([1.0]),
+                     np.array([-np.inf]), np.array([np.inf]))
+
+
+def test_restart_criteria_i_and_ii_at_the_paper_thresholds():
+    """Criteria (i) and (ii) of Sec. 3 at beta_suff = 0.1, beta_nec = 0.9 (beta_art =
+    0.5, checks every 10 iterations) on a closed-form trajectory: the rotating, not
+    monotone, gap of fixed-step PDHG on a 1 x 1 equality-constrained LP with a free
+    variable.  (iii) restarts at 1, 2, 4, ..., 64; (i) at k = 90, where the average's
+    gap is 0.0885 of mu_ref; (ii) at k = 130, where the candidate gap (0.118 of mu_ref)
+    rose above the k = 120 check's; (i) again at 180.  The facts that separate the
+    schedule from plausible misreadings are asserted on the closed form too: at k = 64
+    (a (iii) iteration, not a check) and at k = 70 (the first check after that restart)
+    the candidate gap lies below 0.9 mu_ref and above the last check's, so evaluating
+    (ii) between checks, or keeping the previous candidate gap across a restart, would
+    restart by (ii) there; at k = 30 the gap is 0.41 of mu_ref, so swapped thresholds
+    would restart by (i)."""
+    iters = 200
+    want, ev = _bilinear_1x1_schedule(1.0, 1.0, -1.0, 0.25, 4.0, 10, iters, 0.1, 0.9, 0.5)
+    assert want == BILINEAR_SCHEDULE
+    r = {k: v[0] / v[1] if v[1] else math.nan for k, v in ev.items()}
+    assert r[90] < 0.1 and 0.1 < r[130] <= 0.9 and ev[130][0] > ev[120][0] and r[180] < 0.1
+    assert 0.1 < r[64] <= 0.9 and ev[64][0] > ev[60][0]   # (ii) would hold at the (iii) step
+    assert 0.1 < r[70] <= 0.9 and ev[70][0] > ev[60][0]   # ... and against a stale mu_c_prev
+    assert 0.1 < r[30] <= 0.9                             # (i) with beta 0.9 would fire
+    # every decision is away from its threshold by far more than rounding
+    for k, (mu_c, mu_ref, _, mc, ma) in ev.items():
+        if mu_ref:
+            assert min(abs(mu_c - 0.1 * mu_ref), abs(mu_c - 0.9 * mu_ref)) > 1e-3 * mu_ref, k
+    prm = O.Params(fixed_step=0.25, fixed_omega=4.0, check_period=10, ruiz_iters=0, pc_alpha=0.0,
+                   eps_rel_kkt=-1.0, max_iters=iters, detect_infeasibility=False)
+    res = O.solve(bilinear_instance(), prm, trace_iters=iters)
+    got = [(rec["k"], rec["restart"]) for rec in res.trace if rec["restart"] != O.RESTART_NONE]
+    assert got == BILINEAR_SCHEDULE
+    assert res.stats["restarts"] == [2, 1, 7]
+    # the oracle's normalized gap (bisection on the trust-region multiplier) equals the
+    # closed form at every evaluation
+    for rec in res.trace:
+        if rec["k"] in ev:
+            _, _, _, mc, ma = ev[rec["k"]]
+            assert rec["mu_cur"] == pytest.approx(mc, rel=1e-11), rec["k"]
+            assert rec["mu_avg"] == pytest.approx(ma, rel=1e-11), rec["k"]
+
+
+SECOND_BILINEAR_SCHEDULE = [(1, 3), (2, 3), (4, 3), (8, 3), (16, 3), (32, 3), (48, 1), (69, 2),
+                            (87, 1), (108, 2), (126, 1), (147, 2), (165, 1), (186, 2)]
+
+
+def test_necessary_decay_needs_the_decay_bound():
+    """The same LP with eta = 11/32, omega = 4 and checks every 3 iterations: (i) and (ii)
+    alternate from k = 48 on.  After the (iii) restart at k = 8 the candidate gap rises
+    from the k = 9 check to the k = 12 check but stays above 0.9 mu_ref, so (ii) must
+    not fire there: its decay bound is what holds it back."""
+    iters = 200
+    want, ev = _bilinear_1x1_schedule(1.0, 1.0, -1.0, 11 / 32, 4.0, 3, iters, 0.1, 0.9, 0.5)
+    assert want == SECOND_BILINEAR_SCHEDULE
+    assert ev[12][0] > ev[9][0] and ev[12][0] > 0.9 * ev[12][1] and ev[12][2] == 0
+    for k, (mu_c, mu_ref, _, _, _) in ev.items():
+        if mu_ref:
+            assert min(abs(mu_c - 0.1 * mu_ref), abs(mu_c - 0.9 * mu_ref)) > 1e-3 * mu_ref, k
+    prm = O.Params(fixed_step=11 / 32, fixed_omega=4.0, check_period=3, ruiz_iters=0,
+                   pc_alpha=0.0, eps_rel_kkt=-1.0, max_iters=iters, detect_infeasibility=False)
+    res = O.solve(bilinear_instance(), prm, trace_iters=iters)
+    got = [(rec["k"], rec["restart"]) for rec in res.trace if rec["restart"] != O.RESTART_NONE]
+    assert got == SECOND_BILINEAR_SCHEDULE
+
+
+# min x s.t. x = 2 with eta = omega = 1: the step map (h = 1) is nilpotent, so from
+# z1 = (-1, 4) every iterate is the saddle point (2, 1)
+NILPOTENT_SCHEDULE = [(1, 3), (10, 3)] + [(k, 1) for k in range(12, 40, 3)]
+
+
+def nilpotent_instance():
+    return H.make_lp(np.array([[1.0]]), np.array([1.0]), np.array([2.0]), np.array([2.0]),
+                     np.array([-np.inf]), np.array([np.inf]))
+
+
+def test_necessary_decay_needs_a_strict_increase():
+    """Criterion (ii) asks the candidate gap to have *risen* since the previous check.
+    On min x s.t. x = 2 (free x, eta = omega = 1) PDHG reaches the saddle point (2, 1)
+    exactly at k = 2 and stays; the gap there is exactly 0.  With (i) switched off
+    while mu_ref > 0 (beta_suff = -1), beta_art = 0.9 (so (iii) restarts at k = 1 and
+    10) and checks every 3 iterations, the checks at k = 3, 6, 9 see mu_c = 0 = the
+    previous candidate gap below 0.9 mu_ref = 0.9 mu(z1): no restart, because 0 > 0
+    fails (a non-strict reading restarts at 6).  The restart at 10 makes the saddle
+    point z^{n,0}, so mu_ref = 0 and (i) holds from then on (0 <= -0) at every check."""
+    iters = 40
+    want, ev = _bilinear_1x1_schedule(1.0, 2.0, 1.0, 1.0, 1.0, 3, iters, -1.0, 0.9, 0.9)
+    assert want == NILPOTENT_SCHEDULE
+    assert ev[3][0] == ev[6][0] == ev[9][0] == 0.0 and ev[6][1] > 0.0
+    prm = O.Params(fixed_step=1.0, fixed_omega=1.0, check_period=3, beta_suff=-1.0,
+                   beta_art=0.9, ruiz_iters=0, pc_alpha=0.0, eps_rel_kkt=-1.0, max_iters=iters,
+                   detect_infeasibility=False)
+    res = O.solve(nilpotent_instance(), prm, trace_iters=iters)
+    assert list(res.trace[0]["x"]) == [-1.0] and list(res.trace[0]["y"]) == [4.0]
+    assert all(list(r["x"]) == [2.0] and list(r["y"]) == [1.0] for r in res.trace[1:])
+    got = [(rec["k"], rec["restart"]) for rec in res.trace if rec["restart"] != O.RESTART_NONE]
+    assert got == NILPOTENT_SCHEDULE
+
+
 def test_primal_weight_closed_form():
     """Algorithm 3 with theta = 1/2 is the geometric mean of omega and Dy/Dx; outside
     (eps0, 1/eps0) the weight is kept."""
