@@ -54,7 +54,10 @@ def parse_args():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
                     help="arithmetic of the PDHG loop (fp32 = FP32 bulk, FP64 checks)")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--cpu-baseline", action="store_true",
+                    help="with --no-extras: still run the CPU oracle sample")
     ap.add_argument("--cpu-sample-child", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--points", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -175,28 +178,54 @@ def oracle_sample(inst, iters):
     return time.perf_counter() - t0
 
 
+def oracle_errors(inst, points_path):
+    """The FP64 oracle's optimality measures (kkt_stats, on the unscaled LP) of each
+    returned point saved in ``points_path`` (x_<name>, y_<name> arrays)."""
+    import numpy as np
+    from oracle import pdlp_oracle as O
+
+    pts = np.load(points_path)
+    A = inst.scipy_csr()
+    out = {}
+    for key in pts.files:
+        if not key.startswith("x_"):
+            continue
+        name = key[2:]
+        st = O.kkt_stats(inst, A, pts[key], pts["y_" + name])
+        out[name] = {f: float(st[f]) for f in ("pobj", "dobj", "rel_kkt", "rel_primal", "rel_dual",
+                                                "rel_gap", "primal_res_inf", "dual_res_inf")}
+    return out
+
+
 def cpu_sample_child(args):
     import lpgen
 
     inst = lpgen.config1(scale=args.scale)
     secs = oracle_sample(inst, CPU_SAMPLE_ITERS)
-    print(json.dumps({"secs": secs, "iters": CPU_SAMPLE_ITERS}))
+    res = {"secs": secs, "iters": CPU_SAMPLE_ITERS}
+    if args.points:
+        res["errors"] = oracle_errors(inst, args.points)
+    print(json.dumps(res))
 
 
-def cpu_baseline(args):
+def cpu_baseline(args, points_path=None):
+    """The CPU leg: the oracle timed on a bounded sample of the workload (one thread) and,
+    when ``points_path`` is given, the oracle's FP64 measures of the GPU results."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample-child", "--scale", str(args.scale)]
+    if points_path:
+        cmd += ["--points", points_path]
     r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
     line = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
     if r.returncode != 0 or not line:
         return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
-                "sample": "failed: " + r.stderr[-300:]}
+                "sample": "failed: " + r.stderr[-300:]}, None
     d = json.loads(line[-1])
     return {"value": d["iters"] / d["secs"], "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": (f"{d['iters']} PDHG iterations (Algorithm 2 step, A'y, running sums) of the "
                        f"FP64 numpy/scipy oracle on the same LP with identity scaling, 1 thread, "
-                       f"{d['secs']:.1f} s; preconditioning and periodic checks excluded")}
+                       f"{d['secs']:.1f} s; preconditioning and periodic checks excluded")}, d.get("errors")
 
 
 # ---------------------------------------------------------------------------
@@ -291,7 +320,7 @@ def run_ours(args):
 
     prec = pkg.FP64 if args.precision == "fp64" else pkg.FP32_BULK
 
-    def step(profile=1, n_iters=iters):
+    def step(profile=0, n_iters=iters):
         return pkg.solve(inst.m, inst.n, *d, max_iters=n_iters, eps_rel_kkt=0.0, profile=profile,
                          precision=prec)
 
@@ -299,6 +328,8 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
+    # the timed steps run the library's default path (profile = 0: spans of step attempts
+    # replayed from CUDA graphs, no per-kernel events)
     warmup_launches = 0
     for _ in range(max(args.warmup, 3)):
         warmup_launches += step(n_iters=args.warmup_iters_per_step or iters).stats["kernel_launches"]
@@ -308,25 +339,33 @@ def run_ours(args):
     clk = ClockSampler(local)
     clk.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    agg = {"ms_spmv_a": 0.0, "ms_spmv_at": 0.0, "launches_spmv_a": 0, "launches_spmv_at": 0,
-           "kernel_launches": 0, "iterations": 0}
+    agg = {"kernel_launches": 0, "iterations": 0}
     e0.record(stream)
-    last = None
     for _ in range(args.steps):
         r = step()
         for k in agg:
             agg[k] += r.stats[k]
-        last = r
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
     clocks = clk.stop()
     secs = e0.elapsed_time(e1) / 1e3
-    box_copy = copy_bandwidth_gbs(torch, stream)
     secs_max, total_iters, total_launches = aggregate_over_ranks(
         dist, secs, agg["iterations"], agg["kernel_launches"], "cuda")
     value = total_iters / secs_max
+
+    # per-kernel device times: one separate, untimed solve of the same workload with
+    # profile = 1 (CUDA events around every hot kernel on the launching stream)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    last = step(profile=1)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    prof_secs = p0.elapsed_time(p1) / 1e3
+    agg.update({k: last.stats[k] for k in ("ms_spmv_a", "ms_spmv_at", "launches_spmv_a",
+                                            "launches_spmv_at", "ms_primal")})
+    box_copy = copy_bandwidth_gbs(torch, stream)
 
     # dominant fused SpMV kernel (CUDA events inside the library, on the launching stream)
     st = last.stats
@@ -352,7 +391,10 @@ def run_ours(args):
                 "copy_gbs_this_gpu": box_copy}
     other = {c[0]: {"ms_per_launch": c[1] / c[2], "gbs": c[3] / (c[1] / c[2] / 1e3) / 1e9,
                     "algorithmic_bytes_per_launch": c[3], "launches": c[2],
-                    "share_of_step": c[1] / (1e3 * secs)} for c in cand}
+                    "share_of_instrumented_step": c[1] / (1e3 * prof_secs)} for c in cand}
+    other["primal"] = {"ms_total": agg["ms_primal"],
+                       "share_of_instrumented_step": agg["ms_primal"] / (1e3 * prof_secs)}
+    other["instrumented_step_ms"] = 1e3 * prof_secs
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * secs_max / args.steps,
@@ -361,6 +403,10 @@ def run_ours(args):
            "data": "synthetic",
            "config": {"workload": workload_name(inst), "iters_per_step": iters,
                       "precision": args.precision, "inputs": "HBM-resident (torch CUDA tensors)",
+                      "timed_path": "library default (profile=0): step attempts replayed from "
+                                    "per-run CUDA graphs, no per-kernel events",
+                      "roofline_source": "per-kernel CUDA events of one separate, untimed "
+                                         "solve of the same workload with profile=1",
                       "l2": "no flush: the matrix (A and A' ~1.2 GB FP64) is far larger than L2",
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
            "roofline": roofline, "kernels": other, "clocks": clocks,
@@ -388,13 +434,23 @@ def run_ours(args):
                   "buffers": "pinned host memory via the C ABI (inputs_on_device = 0)"}
 
     if rank == 0 and not args.no_extras:
-        out["time_to_rel_kkt_1e-4"] = time_to_tolerance(pkg, inst, d)
+        points = {}
+        out["time_to_rel_kkt_1e-4"] = time_to_tolerance(pkg, inst, d, points)
         del d
         more_instances(pkg, args.scale, out["time_to_rel_kkt_1e-4"])
         out["polishing_mcf"] = polishing_mcf(pkg)
         out["batch_uneven"] = batch_uneven(pkg)
         out["adjoint_unrolled"] = adjoint_unrolled(pkg)
-        out["cpu_baseline"] = cpu_baseline(args)
+        fd, path = tempfile.mkstemp(suffix=".npz")
+        os.close(fd)
+        np.savez(path, **points)
+        out["cpu_baseline"], errs = cpu_baseline(args, path)
+        os.unlink(path)
+        if errs:
+            for name, e in errs.items():
+                out["time_to_rel_kkt_1e-4"][name]["vs_fp64_oracle"] = e
+    elif rank == 0 and args.cpu_baseline:
+        out["cpu_baseline"], _ = cpu_baseline(args)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -408,9 +464,11 @@ def measure(pkg, inst, d, x, y):
     return pkg.kkt(inst.m, inst.n, *d, x, y)
 
 
-def time_to_tolerance(pkg, inst, d):
+def time_to_tolerance(pkg, inst, d, points=None):
     """FP64 plain vs FP32 bulk to relative KKT 1e-4 on the same GPU; each result's
-    objective and residuals are re-measured in FP64 on the unscaled LP (pdlp_kkt)."""
+    objective and residuals are re-measured in FP64 on the unscaled LP (pdlp_kkt), and
+    the returned points are kept in ``points`` for the FP64 oracle's measures (taken by
+    the CPU leg)."""
     import torch
 
     res = {}
@@ -422,6 +480,9 @@ def time_to_tolerance(pkg, inst, d):
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         ok = measure(pkg, inst, d, r.x, r.y)
+        if points is not None:
+            points["x_" + name] = r.x.cpu().numpy()
+            points["y_" + name] = r.y.cpu().numpy()
         res[name] = {"seconds": wall, "status": r.status_name, "iterations": r.stats["iterations"],
                      "seconds_setup": r.stats["seconds_setup"],
                      "rel_kkt": ok["rel_kkt"], "rel_primal": ok["rel_primal"],
