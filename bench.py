@@ -280,6 +280,26 @@ def copy_bandwidth_gbs(torch, stream):
 
 
 
+def gather_ceilings(pkg, inst, elem_bytes):
+    """pdlp_gather_bench (LSU gathers, the kernels' design) on the access pattern of each
+    sparse product of the workload: entries = nnz, gathered vector of the other side's
+    length, mean row length of the product's matrix; A x' gathers x at columns whose
+    rank frequencies follow the power law of the column degrees (exponent 1/(s-1) for
+    degree exponent s), A'y' gathers y uniformly."""
+    import lpgen
+
+    s_deg = lpgen.zipf_mean_exponent(2, 5000, 10.0)
+    out = {}
+    for key, table, rows, zipf in (("spmv_a", inst.n, inst.m, 1.0 / (s_deg - 1.0)),
+                                   ("spmv_at", inst.m, inst.n, 0.0)):
+        row_len = max(1, int(round(inst.nnz / rows)))
+        r = pkg.gather_bench("lsu", elem_bytes, (table + 3) // 4 * 4, row_len, inst.nnz, zipf, 10)
+        out[key] = {"us": r["us"], "entries_per_s": r["entries_per_s"], "entries": r["entries"],
+                    "table_len": table, "row_len": row_len, "zipf_s": zipf,
+                    "elem_bytes": elem_bytes, "method": "one global load per entry (LSU)"}
+    return out
+
+
 def aggregate_over_ranks(dist, secs, iters, launches, device):
     """Whole-job figures of independent replicas: the slowest rank's seconds and the
     iterations and kernel launches of all ranks (one all_reduce each; works on any
@@ -392,6 +412,13 @@ def run_ours(args):
     other = {c[0]: {"ms_per_launch": c[1] / c[2], "gbs": c[3] / (c[1] / c[2] / 1e3) / 1e9,
                     "algorithmic_bytes_per_launch": c[3], "launches": c[2],
                     "share_of_instrumented_step": c[1] / (1e3 * prof_secs)} for c in cand}
+    # the random-gather ceiling of this GPU for the same access patterns: a SELL-32
+    # product with one gather per entry from a vector of the same length, same number
+    # of entries, mean row length of the kernel's matrix; the A side's columns are
+    # length-sorted with power-law degrees, i.e. rank frequencies ~ r^-(1/(s-1))
+    ceil = gather_ceilings(pkg, inst, 8 if args.precision == "fp64" else 4)
+    roofline["gather_ceiling_us"] = ceil[key]["us"]
+    roofline["frac_of_gather_ceiling"] = ceil[key]["us"] / (per_launch_s * 1e6)
     other["primal"] = {"ms_total": agg["ms_primal"],
                        "share_of_instrumented_step": agg["ms_primal"] / (1e3 * prof_secs)}
     other["instrumented_step_ms"] = 1e3 * prof_secs
@@ -409,7 +436,7 @@ def run_ours(args):
                                          "solve of the same workload with profile=1",
                       "l2": "no flush: the matrix (A and A' ~1.2 GB FP64) is far larger than L2",
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-           "roofline": roofline, "kernels": other, "clocks": clocks,
+           "roofline": roofline, "kernels": other, "gather_ceiling": ceil, "clocks": clocks,
            "gpu_launches": int(total_launches), "warmup_gpu_launches": int(warmup_launches)}
 
     # e2e: host pinned buffers, copies inside the timed region

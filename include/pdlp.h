@@ -315,6 +315,25 @@ int pdlp_unrolled_pdhg_batch(int64_t count, const pdlp_unrolled_problem* problem
 /* Message for the last nonzero return of a call made by this thread. */
 const char* pdlp_last_error(void);
 
+/* Measurement, not part of the solve: the random-gather ceiling of this GPU for the
+ * access pattern of the two sparse products, which Sec. 5 ("Multithreading") finds
+ * memory bound.  It times y = M t for a synthetic SELL-32 matrix M (32-row slices of
+ * row_len entries each, floor(nnz / (32 row_len)) slices) whose entries gather one
+ * element of a vector t of table_len elements at a random index, uniform or (zipf_s >
+ * 0) drawn by rank from a power law P(r) ~ r^-zipf_s (hot indices first, like the
+ * length-sorted columns of a power-law matrix).  method: 0 = one global load per entry
+ * (the design of the solver's kernels), 1 = TMA tile::gather4 of 32-byte rows into
+ * shared memory, 2 = half the warps each way; elem_bytes 8 (4 for method 0 only);
+ * methods 1 and 2 need row_len 8 or 24.  The data are generated on the current device
+ * (cudaMalloc'd for the call, freed before return); the best of reps timed launches
+ * (after one warm-up) is reported.
+ *   out[0] microseconds per launch, out[1] gathered entries per second, out[2] largest
+ *   |y - y_LSU| of methods 1 and 2 against method 0 (0 for method 0), out[3] entries.
+ * Returns 0, PDLP_INVALID_ARGUMENT, PDLP_OUT_OF_MEMORY or PDLP_CUDA_ERROR (also when a
+ * bounded wait for a TMA copy gave up). */
+int pdlp_gather_bench(int method, int elem_bytes, int64_t table_len, int row_len, int64_t nnz,
+                      double zipf_s, int reps, double* out);
+
 #ifdef __cplusplus
 }
 #endif

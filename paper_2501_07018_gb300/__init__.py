@@ -4,5 +4,5 @@ The solver is the CUDA library libpdlp.so behind the C ABI of include/pdlp.h; th
 package only marshals arguments to it (see ``binding``).
 """
 from .binding import (FP32_BULK, FP64, STATUS_NAMES, PdlpError, SolveResult, default_params,  # noqa: F401
-                      kkt, kkt_products_noalloc, load_library, normalized_gap, precondition, solve,
+                      gather_bench, kkt, kkt_products_noalloc, load_library, normalized_gap, precondition, solve,
                       solve_batch, solve_instance)

@@ -145,6 +145,9 @@ def load_library(path: str | None = None):
                                        ctypes.POINTER(Params), P, P, P, P, P, P, P]
     lib.pdlp_unrolled_pdhg.restype = ctypes.c_int
     lib.pdlp_unrolled_pdhg_batch.argtypes = [i64, P, ctypes.POINTER(Params), ctypes.c_int, P]
+    lib.pdlp_gather_bench.argtypes = [ctypes.c_int, ctypes.c_int, i64, ctypes.c_int, i64,
+                                      ctypes.c_double, ctypes.c_int, P]
+    lib.pdlp_gather_bench.restype = ctypes.c_int
     lib.pdlp_unrolled_pdhg_batch.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -481,3 +484,17 @@ def kkt_products_noalloc(m, n, c, lc, uc, lv, uv, x, y, ax, aty, cuda_stream=Non
     _check(lib.pdlp_kkt_products_noalloc(m, n, *[t.data_ptr() if t.numel() else None for t in args],
                                          stream, out.ctypes.data))
     return dict(zip(KKT_FIELDS, out.tolist()))
+
+
+GATHER_METHODS = {"lsu": 0, "tma": 1, "hybrid": 2}
+
+
+def gather_bench(method="lsu", elem_bytes=8, table_len=2_000_000, row_len=24,
+                 nnz=50_000_000, zipf_s=0.0, reps=10) -> dict:
+    """pdlp_gather_bench: the random-gather ceiling of the current GPU for the access
+    pattern of the sparse products (a measurement; the data live on the device)."""
+    lib = load_library()
+    out = np.zeros(4)
+    _check(lib.pdlp_gather_bench(GATHER_METHODS[method], elem_bytes, int(table_len), row_len,
+                                 int(nnz), float(zipf_s), reps, out.ctypes.data))
+    return dict(us=out[0], entries_per_s=out[1], max_diff_vs_lsu=out[2], entries=int(out[3]))

@@ -99,8 +99,10 @@ def test_restart_criteria_i_ii_in_closed_form(pkg, case):
     for r in res.trace:
         if r["k"] in ev:
             _, _, _, mc, ma = ev[r["k"]]
-            assert r["mu_cur"] == pytest.approx(mc, rel=1e-10, abs=1e-300), r["k"]
-            assert r["mu_avg"] == pytest.approx(ma, rel=1e-10, abs=1e-300), r["k"]
+            # the iterates drift from the closed form by rounding (~1e-16 of |z| ~ 1), so
+            # late, small gaps (1e-6) are compared to an absolute 1e-14
+            assert r["mu_cur"] == pytest.approx(mc, rel=1e-9, abs=1e-14), r["k"]
+            assert r["mu_avg"] == pytest.approx(ma, rel=1e-9, abs=1e-14), r["k"]
 
 
 def test_fixed_step_and_weight_rejected_when_invalid(pkg):
@@ -143,6 +145,36 @@ def test_trace_parity_first_100_iterations(pkg, name):
         if not math.isnan(oc):
             assert abs(gc - oc) <= 1e-9 * max(1e-12, abs(oc)) + 1e-14
             assert abs(ga - oa) <= 1e-9 * max(1e-12, abs(oa)) + 1e-14
+
+
+def _named_instance(name):
+    if name == "config0":
+        return lpgen.config0()
+    if name == "edge":
+        return GH.edge_instance()
+    if name == "edge_long":
+        return GH.edge_instance(seed=12, m=12000, n=24000, dense_row_nnz=20000,
+                                dense_col_nnz=10000)
+    if name == "mcf":
+        return lpgen.multicommodity_flow_lp(200, 2000, 10, seed=7)
+    return lpgen.config1(scale=0.002)
+
+
+@pytest.mark.parametrize("name", ["config0", "edge", "edge_long", "powerlaw", "mcf"])
+def test_returned_point_parity_without_trace(pkg, name):
+    """The production path (no trace: many step attempts launched between the
+    iterations where the host reads the device state) returns, at the 100-iteration
+    limit, the oracle's candidate point (unscaled) to the trace tolerance, with the
+    same restarts."""
+    inst = _named_instance(name)
+    res = pkg.solve_instance(inst, max_iters=100, eps_rel_kkt=0.0)
+    ora = O.solve(inst, O.Params(max_iters=100, eps_rel_kkt=0.0))
+    assert res.status == ora.status == O.ITERATION_LIMIT
+    assert res.stats["restarts"] == list(ora.stats["restarts"])
+    zo = np.concatenate([ora.x, ora.y])
+    zg = np.concatenate([res.x, res.y])
+    err = float(np.max(np.abs(zg - zo))) / max(1.0, float(np.max(np.abs(zo))))
+    assert err <= TRACE_TOL, err
 
 
 @pytest.mark.parametrize("name", ["config0", "edge"])
