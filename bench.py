@@ -283,19 +283,21 @@ def copy_bandwidth_gbs(torch, stream):
 def gather_ceilings(pkg, inst, elem_bytes):
     """pdlp_gather_bench (LSU gathers, the kernels' design) on the access pattern of each
     sparse product of the workload: entries = nnz, gathered vector of the other side's
-    length, mean row length of the product's matrix; A x' gathers x at columns whose
-    rank frequencies follow the power law of the column degrees (exponent 1/(s-1) for
-    degree exponent s), A'y' gathers y uniformly."""
+    length, mean row length of the product's matrix; A x' gathers x at the columns of a
+    matrix with the workload's power-law column degrees (truncated to [2, 5000], numbered
+    by decreasing degree), A'y' gathers y uniformly (the rows' entries are uniform)."""
     import lpgen
 
     s_deg = lpgen.zipf_mean_exponent(2, 5000, 10.0)
     out = {}
-    for key, table, rows, zipf in (("spmv_a", inst.n, inst.m, 1.0 / (s_deg - 1.0)),
-                                   ("spmv_at", inst.m, inst.n, 0.0)):
+    for key, table, rows, deg in (("spmv_a", inst.n, inst.m, s_deg), ("spmv_at", inst.m, inst.n, 0.0)):
         row_len = max(1, int(round(inst.nnz / rows)))
-        r = pkg.gather_bench("lsu", elem_bytes, (table + 3) // 4 * 4, row_len, inst.nnz, zipf, 10)
+        r = pkg.gather_bench("lsu", elem_bytes, (table + 3) // 4 * 4, row_len, inst.nnz, deg,
+                             2.0, 5000.0, 10)
         out[key] = {"us": r["us"], "entries_per_s": r["entries_per_s"], "entries": r["entries"],
-                    "table_len": table, "row_len": row_len, "zipf_s": zipf,
+                    "table_len": table, "row_len": row_len,
+                    "columns": (f"power-law degrees s={deg:.3f} on [2, 5000], sorted" if deg > 0
+                                else "uniform"),
                     "elem_bytes": elem_bytes, "method": "one global load per entry (LSU)"}
     return out
 
@@ -613,7 +615,9 @@ def adjoint_unrolled(pkg, count=256, K=2000, every=50, concurrency=16):
     column, x_target ~ U[0,10]) through pdlp_unrolled_pdhg_batch: K fixed-step PDHG steps
     (eta = 0.9 / sqrt(||A||_1 ||A||_inf) <= 0.9 / ||A||_2), then the adjoint of
     ||x_K - x_target||^2 with checkpoints every `every` steps; wall clock of the forward
-    batch and of the forward + reverse batch, host arrays."""
+    batch and of the forward + reverse batch, host arrays, with the FP32 forward (FP64
+    reverse pass) and with FP64 throughout, and the relative l2 distance of the FP32-
+    forward gradients from the FP64 ones."""
     import numpy as np
 
     import lpgen
@@ -628,21 +632,27 @@ def adjoint_unrolled(pkg, count=256, K=2000, every=50, concurrency=16):
         ai = float(abs(A).sum(axis=1).max())
         items.append(dict(lp=inst, K=K, eta=0.9 / np.sqrt(a1 * ai), omega=1.0,
                           checkpoint_every=every, target=rng.uniform(0.0, 10.0, inst.n)))
-    fw = [dict(it) for it in items]
-    t0 = time.perf_counter()
-    got = binding.unrolled_pdhg_batch(fw, concurrency=concurrency)
-    t_fw = time.perf_counter() - t0
-    for it, (_, x, _, _) in zip(items, got):
-        it["gx"] = 2.0 * (x - it["target"])
-        it["gy"] = np.zeros(it["lp"].m)
-    t0 = time.perf_counter()
-    got = binding.unrolled_pdhg_batch(items, concurrency=concurrency)
-    t_fb = time.perf_counter() - t0
-    ok = sum(1 for g in got if g[0] == 0 and np.all(np.isfinite(g[3]["c"])))
-    return {"workload": f"{count} LPs m=2000 n=5000 (8 entries per column), K={K} steps, "
-                        f"checkpoint every {every}, {concurrency} in flight, host arrays",
-            "forward_s": t_fw, "forward_backward_s": t_fb, "lps_per_s_forward_backward": count / t_fb,
-            "ok": ok}
+    out = {"workload": f"{count} LPs m=2000 n=5000 (8 entries per column), K={K} steps, "
+                       f"checkpoint every {every}, {concurrency} in flight, host arrays"}
+    grads = {}
+    for name, prec in (("fp32_forward", binding.FP32_BULK), ("fp64", binding.FP64)):
+        fw = [dict(it) for it in items]
+        t0 = time.perf_counter()
+        got = binding.unrolled_pdhg_batch(fw, concurrency=concurrency, precision=prec)
+        t_fw = time.perf_counter() - t0
+        bw = []
+        for it, (_, x, _, _) in zip(items, got):
+            bw.append(dict(it, gx=2.0 * (x - it["target"]), gy=np.zeros(it["lp"].m)))
+        t0 = time.perf_counter()
+        got = binding.unrolled_pdhg_batch(bw, concurrency=concurrency, precision=prec)
+        t_fb = time.perf_counter() - t0
+        ok = sum(1 for g in got if g[0] == 0 and np.all(np.isfinite(g[3]["c"])))
+        grads[name] = [g[3]["c"] for g in got[:4]]
+        out[name] = {"forward_s": t_fw, "forward_backward_s": t_fb,
+                     "lps_per_s_forward_backward": count / t_fb, "ok": ok}
+    out["grad_c_rel_l2_fp32_vs_fp64_first4"] = [
+        float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(grads["fp32_forward"], grads["fp64"])]
+    return out
 
 
 def main():

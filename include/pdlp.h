@@ -236,8 +236,10 @@ int pdlp_kkt(int64_t m, int64_t n, const pdlp_csr* A, const double* c, const dou
  * result live in one fixed file-scope device array of about 74 KB, which every GPU
  * that loads the library keeps until the process exits; its size does not depend on
  * m or n.  The first call on a device looks the array's address up
- * (cudaGetSymbolAddress) and caches it; make that first call before any stream
- * capture.  Every call clears the counter and overwrites the rest.  All calls share
+ * (cudaGetSymbolAddress) and caches it per device index; make that first call before
+ * any stream capture.  The cached address belongs to the context that was current at
+ * that first call, normally the device's primary context (the runtime API's); callers
+ * that switch to other contexts of the same device must not use this entry point.  Every call clears the counter and overwrites the rest.  All calls share
  * the one array: calls whose work overlaps on the GPU (other streams, other host
  * threads) race and give wrong results, so serialize them.  The call blocks until
  * its result is in out.  Returns 0, PDLP_INVALID_ARGUMENT or PDLP_CUDA_ERROR. */
@@ -280,10 +282,14 @@ int pdlp_solve_batch(int64_t count, const pdlp_problem* problems, const pdlp_par
  * grad_* arrays (the vector-Jacobian product of the unrolled map; at a clamp boundary
  * the derivative of the inside branch is taken; infinite bounds get 0), by a reverse
  * pass that recomputes the iterates from checkpoints stored every checkpoint_every
- * steps (<= 0: 50): memory 2(m+n)(K/checkpoint_every + checkpoint_every + 2) doubles,
- * time about 3x the forward pass.  FP64.  params: inputs_on_device (host or device
- * arrays, outputs alike) and cuda_stream are used; the rest is ignored.  Returns 0 or
- * a negative error code. */
+ * steps (<= 0: 50): memory 2(m+n)(K/checkpoint_every + checkpoint_every + 2) values,
+ * time about 3x the forward pass.  params->precision: PDLP_FP64 runs everything in
+ * FP64; PDLP_FP32_BULK runs the forward iteration (matrix values, iterates, products,
+ * checkpoints) in FP32 with steps rounded to FP32, and the reverse pass in FP64 (FP64
+ * matrix and adjoints) with each clamp branch taken as the FP32 forward took it: the
+ * gradient of the exact map along the FP32 trajectory.  inputs_on_device (host or
+ * device arrays, outputs alike) and cuda_stream are used too; the rest is ignored.
+ * Returns 0 or a negative error code. */
 int pdlp_unrolled_pdhg(int64_t m, int64_t n, const pdlp_csr* A, const double* c,
                        const double* lc, const double* uc, const double* lv, const double* uv,
                        int64_t K, double eta, double omega, int64_t checkpoint_every,
@@ -319,9 +325,10 @@ const char* pdlp_last_error(void);
  * access pattern of the two sparse products, which Sec. 5 ("Multithreading") finds
  * memory bound.  It times y = M t for a synthetic SELL-32 matrix M (32-row slices of
  * row_len entries each, floor(nnz / (32 row_len)) slices) whose entries gather one
- * element of a vector t of table_len elements at a random index, uniform or (zipf_s >
- * 0) drawn by rank from a power law P(r) ~ r^-zipf_s (hot indices first, like the
- * length-sorted columns of a power-law matrix).  method: 0 = one global load per entry
+ * element of a vector t of table_len elements: at uniform random indices (degree_s <=
+ * 0), or (degree_s > 1, != 2) at the columns of a matrix whose table_len columns have
+ * degrees from the truncated power law P(d) ~ d^-degree_s on [dmin, dmax], numbered by
+ * decreasing degree as the solver numbers them.  method: 0 = one global load per entry
  * (the design of the solver's kernels), 1 = TMA tile::gather4 of 32-byte rows into
  * shared memory, 2 = half the warps each way; elem_bytes 8 (4 for method 0 only);
  * methods 1 and 2 need row_len 8 or 24.  The data are generated on the current device
@@ -332,7 +339,7 @@ const char* pdlp_last_error(void);
  * Returns 0, PDLP_INVALID_ARGUMENT, PDLP_OUT_OF_MEMORY or PDLP_CUDA_ERROR (also when a
  * bounded wait for a TMA copy gave up). */
 int pdlp_gather_bench(int method, int elem_bytes, int64_t table_len, int row_len, int64_t nnz,
-                      double zipf_s, int reps, double* out);
+                      double degree_s, double dmin, double dmax, int reps, double* out);
 
 #ifdef __cplusplus
 }

@@ -146,7 +146,8 @@ def load_library(path: str | None = None):
     lib.pdlp_unrolled_pdhg.restype = ctypes.c_int
     lib.pdlp_unrolled_pdhg_batch.argtypes = [i64, P, ctypes.POINTER(Params), ctypes.c_int, P]
     lib.pdlp_gather_bench.argtypes = [ctypes.c_int, ctypes.c_int, i64, ctypes.c_int, i64,
-                                      ctypes.c_double, ctypes.c_int, P]
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_int, P]
     lib.pdlp_gather_bench.restype = ctypes.c_int
     lib.pdlp_unrolled_pdhg_batch.restype = ctypes.c_int
     _lib = lib
@@ -490,11 +491,14 @@ GATHER_METHODS = {"lsu": 0, "tma": 1, "hybrid": 2}
 
 
 def gather_bench(method="lsu", elem_bytes=8, table_len=2_000_000, row_len=24,
-                 nnz=50_000_000, zipf_s=0.0, reps=10) -> dict:
+                 nnz=50_000_000, degree_s=0.0, dmin=2.0, dmax=5000.0, reps=10) -> dict:
     """pdlp_gather_bench: the random-gather ceiling of the current GPU for the access
-    pattern of the sparse products (a measurement; the data live on the device)."""
+    pattern of the sparse products (a measurement; the data live on the device).
+    degree_s <= 0: uniform indices; > 1: columns of a matrix with power-law degrees on
+    [dmin, dmax], numbered by decreasing degree."""
     lib = load_library()
     out = np.zeros(4)
     _check(lib.pdlp_gather_bench(GATHER_METHODS[method], elem_bytes, int(table_len), row_len,
-                                 int(nnz), float(zipf_s), reps, out.ctypes.data))
+                                 int(nnz), float(degree_s), float(dmin), float(dmax), reps,
+                                 out.ctypes.data))
     return dict(us=out[0], entries_per_s=out[1], max_diff_vs_lsu=out[2], entries=int(out[3]))

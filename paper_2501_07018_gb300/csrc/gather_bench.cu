@@ -10,8 +10,9 @@
 //             (viewed as [len/4][4]) per instruction into shared memory, completion on an
 //             mbarrier, double-buffered per warp;
 //   method 2  half the warps of each CTA gather through the LSU, half through TMA.
-// Column indices are uniform on [0, len) or drawn by rank from a power law (hot
-// columns first, like the length-sorted columns of a power-law matrix).  The data are
+// Column indices are uniform on [0, len), or those of the entries of a matrix with
+// power-law column degrees, columns numbered by decreasing degree (as the solver's
+// renumbering leaves them).  The data are
 // generated on the device from a counter-based hash; nothing here is part of the solver.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -41,10 +42,18 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 }
 __device__ __forceinline__ double unit(uint64_t h) { return (double)(h >> 11) * 0x1.0p-53; }
 
-// entry e: column uniform on [0, len) (s <= 0) or by rank from P(rank r) ~ r^-s
-// (continuous inverse transform), value in [-0.5, 0.5)
+// Entry e: column uniform on [0, len) (s <= 0), or, for s > 1, the column of a matrix
+// whose len columns have degrees from the truncated power law P(d) ~ d^-s on [dmin,
+// dmax], numbered by decreasing degree, each entry drawn with probability proportional
+// to its column's degree.  Column j's degree is the law's quantile at u = 1 - (j + 1/2)
+// / len, d(u) = (a + u b)^(1/(1-s)) with a = dmin^(1-s), b = dmax^(1-s) - a; the
+// cumulative degree of the columns past u is len (F(1) - F(u)) with F(u) = (a + u b)^g
+// / (b g), g = (2-s)/(1-s), so a uniform share of the total degree inverts in closed
+// form.  Values are uniform in [-0.5, 0.5).
 __global__ void k_gb_fill(int32_t* col, double* val64, float* val32, int64_t nnz, int64_t len,
-                          double s, uint64_t seed) {
+                          double s, double dmin, double dmax, uint64_t seed) {
+  const double a = pow(dmin, 1.0 - s), b = pow(dmax, 1.0 - s) - a, g = (2.0 - s) / (1.0 - s);
+  const double F1 = pow(a + b, g) / (b * g), F0 = pow(a, g) / (b * g);
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
        e += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t h = mix64(seed ^ (uint64_t)e);
@@ -52,10 +61,9 @@ __global__ void k_gb_fill(int32_t* col, double* val64, float* val32, int64_t nnz
     if (s <= 0.0) {
       c = (int64_t)(unit(h) * (double)len);
     } else {
-      const double u = unit(mix64(h));
-      const double a = 1.0 - s;  // s != 1
-      const double r = pow((pow((double)len + 1.0, a) - 1.0) * u + 1.0, 1.0 / a);
-      c = (int64_t)r - 1;
+      const double w = unit(mix64(h)) * (F1 - F0);  // degree share past the column
+      const double u = (pow((F1 - w) * b * g, 1.0 / g) - a) / b;
+      c = (int64_t)((1.0 - u) * (double)len);
     }
     c = c < 0 ? 0 : (c >= len ? len - 1 : c);
     col[e] = (int32_t)c;
@@ -85,8 +93,8 @@ __device__ __forceinline__ T gb_slice_lsu(const int32_t* __restrict__ cp, const 
 #pragma unroll
     for (int u = 0; u < kGbBatch; ++u) {
       const bool in = k0 + u < L;
-      c[u] = in ? cp[32 * (k0 + u)] : 0;
-      v[u] = in ? vp[32 * (k0 + u)] : (T)0;
+      c[u] = in ? __ldcs(cp + 32 * (k0 + u)) : 0;  // streamed, evict-first
+      v[u] = in ? __ldcs(vp + 32 * (k0 + u)) : (T)0;
     }
 #pragma unroll
     for (int u = 0; u < kGbBatch; ++u) x[u] = (k0 + u < L) ? tab[c[u]] : (T)0;
@@ -161,7 +169,7 @@ __device__ __forceinline__ double gb_slice_tma(const int32_t* __restrict__ cp,
       if (lane == 0) mbar_expect_tx(&bars[nb], 32u * 128u);
       __syncwarp();
 #pragma unroll
-      for (int u = 0; u < 4; ++u) cl[4 * nx + u] = cp[32 * (4 * nx + u)];
+      for (int u = 0; u < 4; ++u) cl[4 * nx + u] = __ldcs(cp + 32 * (4 * nx + u));
       tma_gather4(base + (size_t)(nb * 32 + lane) * 128, map, cl[4 * nx] >> 2,
                   cl[4 * nx + 1] >> 2, cl[4 * nx + 2] >> 2, cl[4 * nx + 3] >> 2, &bars[nb]);
     }
@@ -177,7 +185,7 @@ __device__ __forceinline__ double gb_slice_tma(const int32_t* __restrict__ cp,
     for (int u = 0; u < 4; ++u) {
       const int c = cl[4 * st + u];
       const double xv = *reinterpret_cast<const double*>(slot + 32 * u + 8 * (c & 3));
-      acc = fma(vp[32 * (4 * st + u)], xv, acc);
+      acc = fma(__ldcs(vp + 32 * (4 * st + u)), xv, acc);
     }
     __syncwarp();
   }
@@ -311,7 +319,8 @@ double max_abs_diff(const T* a, const T* b, int64_t len) {
 }  // namespace pdlp
 
 extern "C" int pdlp_gather_bench(int method, int elem_bytes, int64_t table_len, int row_len,
-                                 int64_t nnz, double zipf_s, int reps, double* out) {
+                                 int64_t nnz, double degree_s, double dmin, double dmax,
+                                 int reps, double* out) {
   using namespace pdlp;
   try {
     if (!out) throw PdlpError(-1, "pdlp_gather_bench: out is NULL");
@@ -322,8 +331,10 @@ extern "C" int pdlp_gather_bench(int method, int elem_bytes, int64_t table_len, 
       throw PdlpError(-1, "pdlp_gather_bench: table_len must be a multiple of 4 in [4, 2^31]");
     if (method > 0 ? (row_len != 8 && row_len != 24) : (row_len < 1 || row_len > 4096))
       throw PdlpError(-1, "pdlp_gather_bench: row_len must be 8 or 24 for TMA, 1..4096 for LSU");
-    if (reps < 1 || zipf_s == 1.0 || std::isnan(zipf_s))
-      throw PdlpError(-1, "pdlp_gather_bench: reps >= 1 and zipf_s != 1 required");
+    if (reps < 1 || std::isnan(degree_s) || (degree_s > 0.0 && !(degree_s > 1.0 && degree_s != 2.0 &&
+                                                                  dmin >= 1.0 && dmax > dmin)))
+      throw PdlpError(-1, "pdlp_gather_bench: reps >= 1; degree_s <= 0, or degree_s > 1, != 2 with "
+                          "1 <= dmin < dmax");
     const int64_t nslices = nnz / (32 * (int64_t)row_len);
     if (nslices < 1 || nslices > ((int64_t)1 << 30))
       throw PdlpError(-1, "pdlp_gather_bench: nnz must hold 1 .. 2^30 slices of 32 rows");
@@ -347,7 +358,8 @@ extern "C" int pdlp_gather_bench(int method, int elem_bytes, int64_t table_len, 
       float* val = B.alloc<float>(ent);
       float* tab = B.alloc<float>(table_len);
       float* y = B.alloc<float>(rows);
-      k_gb_fill<<<fill_grid, 256, 0, s>>>(col, nullptr, val, ent, table_len, zipf_s, 0x1234567ULL);
+      k_gb_fill<<<fill_grid, 256, 0, s>>>(col, nullptr, val, ent, table_len, degree_s, dmin, dmax,
+                                           0x1234567ULL);
       k_gb_table<<<fill_grid, 256, 0, s>>>(nullptr, tab, table_len, 0x7654321ULL);
       PDLP_CUDA_CHECK(cudaGetLastError());
       CUtensorMap none{};
@@ -357,7 +369,8 @@ extern "C" int pdlp_gather_bench(int method, int elem_bytes, int64_t table_len, 
       double* tab = B.alloc<double>(table_len);
       double* y = B.alloc<double>(rows);
       double* yref = B.alloc<double>(rows);
-      k_gb_fill<<<fill_grid, 256, 0, s>>>(col, val, nullptr, ent, table_len, zipf_s, 0x1234567ULL);
+      k_gb_fill<<<fill_grid, 256, 0, s>>>(col, val, nullptr, ent, table_len, degree_s, dmin, dmax,
+                                           0x1234567ULL);
       k_gb_table<<<fill_grid, 256, 0, s>>>(tab, nullptr, table_len, 0x7654321ULL);
       PDLP_CUDA_CHECK(cudaGetLastError());
       CUtensorMap map{};

@@ -102,7 +102,8 @@ __global__ void __launch_bounds__(kThreads)
 std::mutex g_na_mutex;
 double* g_na_ptr[kNaMaxDevices] = {};
 
-// Device address of the scratch array on the current device (looked up once).
+// Device address of the scratch array on the current device, looked up once per device
+// index: the address in the context current at that first call (normally the primary one).
 cudaError_t scratch_address(int dev, double** out) {
   std::lock_guard<std::mutex> lock(g_na_mutex);
   if (!g_na_ptr[dev]) {

@@ -314,7 +314,9 @@ __global__ void __launch_bounds__(kSpmvThreads, PDLP_SPMV_MINB(T)) k_spmv(SpmvAr
       const int L = M.slice_len[sl];
       const int32_t* __restrict__ cp = M.sell_col + M.slice_ptr[sl] + lane;
       const T* __restrict__ vp = M.sell_val + M.slice_ptr[sl] + lane;
-      // two independent FMA chains (even / odd entries) for instruction-level parallelism
+      // the matrix is streamed with evict-first loads (ld.global.cs), so that L1 and L2
+      // keep the gathered vector; two independent FMA chains (even / odd entries) for
+      // instruction-level parallelism
       T acc_e = (T)0, acc_o = (T)0;
       constexpr int kBatch = batch_of<T>();
       for (int k0 = 0; k0 < L; k0 += kBatch) {
@@ -323,8 +325,8 @@ __global__ void __launch_bounds__(kSpmvThreads, PDLP_SPMV_MINB(T)) k_spmv(SpmvAr
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
           const bool in = k0 + u < L;
-          cr[u] = in ? cp[32 * (k0 + u)] : 0;
-          vr[u] = in ? vp[32 * (k0 + u)] : (T)0;
+          cr[u] = in ? __ldcs(cp + 32 * (k0 + u)) : 0;
+          vr[u] = in ? __ldcs(vp + 32 * (k0 + u)) : (T)0;
         }
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) xr[u] = (k0 + u < L) ? src[cr[u]] : (T)0;
@@ -353,7 +355,7 @@ __global__ void __launch_bounds__(kSpmvThreads, PDLP_SPMV_MINB(T)) k_spmv(SpmvAr
       const T* __restrict__ valp = M.val;
       T acc = (T)0;
 #pragma unroll 4
-      for (int64_t p = pb + lane; p < pe; p += 32) acc = fma(valp[p], src[colp[p]], acc);
+      for (int64_t p = pb + lane; p < pe; p += 32) acc = fma(__ldcs(valp + p), src[__ldcs(colp + p)], acc);
       const double part = warp_sum((double)acc);
       // a row of one chunk is finished here; otherwise the last of its chunks to
       // arrive adds the chunk sums (lane q holds chunk q; fixed tree over lanes)

@@ -1595,8 +1595,21 @@ int pdlp_unrolled_pdhg(int64_t m, int64_t n, const pdlp_csr* A, const double* c,
     UnrolledGrads G{dev_out(grad_c, n), dev_out(grad_lc, m), dev_out(grad_uc, m),
                     dev_out(grad_lv, n), dev_out(grad_uv, n)};
     if (gx && m == 0) dgy = nullptr;
-    unrolled_pdhg_run(arena, U, K, checkpoint_every > 0 ? checkpoint_every : 50, dgx, dgy, dx,
-                      dy, gx ? &G : nullptr, s);
+    const int64_t every = checkpoint_every > 0 ? checkpoint_every : 50;
+    if (prm.precision == PDLP_FP32_BULK) {
+      // FP32 forward: the same renumbered LP with FP32 values and vectors (identity
+      // scaling leaves the staged values as given); the reverse pass stays FP64
+      Problem<float> P32;
+      build_problem<float>(arena, in, d, 0, 0.0, P32, s);
+      const UnrolledFwd<float> F{P32.A, P32.AT, P32.c, P32.lc, P32.uc, P32.lv, P32.uv,
+                                 (float)(eta / omega), (float)(eta * omega),
+                                 spmv_grid<float>(P32.A, kEpiPlain), spmv_grid<float>(P32.AT, kEpiPlain)};
+      unrolled_pdhg_run<float>(arena, U, F, K, every, dgx, dgy, dx, dy, gx ? &G : nullptr, s);
+    } else {
+      const UnrolledFwd<double> F{P.A, P.AT, P.c, P.lc, P.uc, P.lv, P.uv, U.tau, U.sigma,
+                                  U.grid_a, U.grid_at};
+      unrolled_pdhg_run<double>(arena, U, F, K, every, dgx, dgy, dx, dy, gx ? &G : nullptr, s);
+    }
     if (!in.on_device) {
       auto back = [&](double* h, const double* dptr, int64_t len) {
         if (h && len > 0)

@@ -67,6 +67,70 @@ def test_gradients_match_oracle_for_every_checkpoint_spacing(pkg, seed):
                     assert np.array_equal(g[k], ref[2][k]), (k, every)
 
 
+@pytest.mark.parametrize("k", [0, 1])
+def test_differentiable_batch_shape_matches_oracle(pkg, k):
+    """The differentiable-batch shape at full size: an LP of 2000 rows x 5000 columns
+    with 8 N(0,1) entries per column, K = 2000 fixed steps eta = 0.9 /
+    sqrt(||A||_1 ||A||_inf) (<= 0.9 / ||A||_2), checkpoints every 50, loss
+    ||x_K - x_target||^2 with x_target ~ U[0,10]: x_K, y_K and the gradients with
+    respect to c, lc, uc, lv, uv equal the oracle's reverse-mode derivative element by
+    element (1e-9 relative to the largest entry)."""
+    import lpgen
+
+    rng = np.random.default_rng(lpgen.config_seed(3) + k)
+    inst = lpgen.random_lp(2000, 5000, 8, seed=lpgen.config_seed(3, k))
+    A = inst.scipy_csr()
+    eta = 0.9 / np.sqrt(float(abs(A).sum(axis=0).max()) * float(abs(A).sum(axis=1).max()))
+    K = 2000
+    target = rng.uniform(0.0, 10.0, inst.n)
+    xK = O.unrolled_pdhg(inst, K, eta, 1.0)[K][0]
+    gx, gy = 2.0 * (xK - target), np.zeros(inst.m)
+    xo, yo, go = O.unrolled_pdhg_vjp(inst, K, eta, 1.0, gx, gy)
+    x, y, g = _run(pkg, inst, K, eta, 1.0, gx, gy, 50)
+    assert _close(x, xo) and _close(y, yo)
+    for key in KEYS:
+        assert _close(g[key], go[key]), key
+
+
+def test_fp32_forward_with_fp64_gradient(pkg):
+    """FP32 forward (precision = FP32 bulk: matrix, iterates, products and checkpoints in
+    FP32) with the FP64 reverse pass, on the differentiable-batch shape (2000 x 5000, 8
+    entries per column, K = 2000, checkpoints every 50): x_K is the FP64 oracle's to FP32
+    accuracy, and the gradients agree with the FP64 oracle's reverse-mode derivative in
+    direction and size (the reverse pass follows the FP32 trajectory's clamp branches,
+    which differ from the FP64 trajectory's only where an iterate sits within rounding of
+    a bound); the FP32 and FP64 forward passes of the library both run through the C ABI."""
+    import lpgen
+
+    rng = np.random.default_rng(lpgen.config_seed(3))
+    inst = lpgen.random_lp(2000, 5000, 8, seed=lpgen.config_seed(3, 0))
+    A = inst.scipy_csr()
+    eta = 0.9 / np.sqrt(float(abs(A).sum(axis=0).max()) * float(abs(A).sum(axis=1).max()))
+    K = 2000
+    target = rng.uniform(0.0, 10.0, inst.n)
+    xK = O.unrolled_pdhg(inst, K, eta, 1.0)[K][0]
+    gx, gy = 2.0 * (xK - target), np.zeros(inst.m)
+    xo, yo, go = O.unrolled_pdhg_vjp(inst, K, eta, 1.0, gx, gy)
+    x, y, g = pkg.binding.unrolled_pdhg(inst.m, inst.n, inst.row_ptr, inst.col_idx, inst.val,
+                                        inst.c, inst.lc, inst.uc, inst.lv, inst.uv, K, eta, 1.0,
+                                        gx=gx, gy=gy, checkpoint_every=50, precision=pkg.FP32_BULK)
+    ex = float(np.max(np.abs(x - xo))) / max(1.0, float(np.max(np.abs(xo))))
+    ey = float(np.max(np.abs(y - yo))) / max(1.0, float(np.max(np.abs(yo))))
+    print(f"FP32 forward: x_K error {ex:.2e}, y_K error {ey:.2e}")
+    assert ex <= 1e-4 and ey <= 1e-4
+    for key in KEYS:
+        a, b = g[key], go[key]
+        nb = float(np.linalg.norm(b))
+        if nb == 0.0:
+            assert float(np.linalg.norm(a)) == 0.0, key
+            continue
+        rel = float(np.linalg.norm(a - b)) / nb
+        cos = float(a @ b) / (float(np.linalg.norm(a)) * nb)
+        frac = float(np.mean(np.abs(a - b) <= 1e-4 * max(1.0, float(np.max(np.abs(b))))))
+        print(f"  grad {key}: relative l2 error {rel:.2e}, cosine {cos:.8f}, entries within 1e-4: {frac:.4f}")
+        assert rel <= 1e-2 and cos >= 0.9999, key
+
+
 def test_gradients_match_central_differences_of_the_gpu_forward(pkg):
     import dataclasses
 

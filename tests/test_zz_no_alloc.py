@@ -1,6 +1,7 @@
 """The allocation-free entry point pdlp_kkt_products_noalloc, checked through the C ABI
-against pdlp_kkt on the same point, on two calls in a row (the second call must not
-see the first call's leftovers in the shared scratch array).
+against pdlp_kkt on the same point and against the FP64 oracle's measures (kkt_stats),
+on two calls in a row (the second call must not see the first call's leftovers in the
+shared scratch array).
 
 It is for callers that cannot let a library allocate device memory while they run
 (their own pool owns the device, or an allocation could stall a latency-bound loop);
@@ -11,6 +12,7 @@ import numpy as np
 import pytest
 
 import lpgen
+from oracle import pdlp_oracle as O
 from tests import gpu_helpers as GH
 
 pytestmark = pytest.mark.gpu
@@ -60,6 +62,10 @@ def test_noalloc_matches_kkt_twice(pkg, name):
         torch.cuda.synchronize()
         for k, v in ref.items():
             assert abs(got[k] - v) <= 1e-11 * max(1.0, abs(v)), (call, k, got[k], v)
+        ora = O.kkt_stats(inst, A, x, y)
+        for k in ("rel_kkt", "rel_primal", "rel_dual", "rel_gap", "pobj", "dobj",
+                  "primal_res_inf", "dual_res_inf"):
+            assert abs(got[k] - ora[k]) <= 1e-10 * max(1.0, abs(ora[k])), (call, k, got[k], ora[k])
         results.append(got)
     assert results[0] != results[1]  # two different points, no stale scratch
 
