@@ -363,10 +363,12 @@ def run_ours(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     agg = {"kernel_launches": 0, "iterations": 0}
     e0.record(stream)
+    timed = None
     for _ in range(args.steps):
         r = step()
         for k in agg:
             agg[k] += r.stats[k]
+        timed = r
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -424,6 +426,12 @@ def run_ours(args):
     other["primal"] = {"ms_total": agg["ms_primal"],
                        "share_of_instrumented_step": agg["ms_primal"] / (1e3 * prof_secs)}
     other["instrumented_step_ms"] = 1e3 * prof_secs
+    ts = timed.stats
+    other["checks_of_last_timed_step"] = {
+        "ms_gap": ts["ms_gap"], "ms_kkt": ts["ms_kkt"], "ms_infeas": ts["ms_infeas"],
+        "ms_checks": ts["ms_checks"], "evaluations": ts["evaluations"], "gap_evals": ts["gap_evals"],
+        "share_of_step": ts["ms_checks"] / (1e3 * secs / args.steps),
+        "note": "host wall time of the checks, device work and the synchronisations they need"}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * secs_max / args.steps,

@@ -175,6 +175,11 @@ typedef struct {
   int64_t polish_accepted_k; /* k of the pause whose pair was returned, else 0     */
   int64_t device_bytes;    /* device memory the call allocated (stream-ordered; all of
                               it is held until the call returns, so this is its peak) */
+  /* wall-clock milliseconds of the periodic checks (device work and the host
+     synchronisations they need): normalized duality gaps, KKT measures, infeasibility
+     tests, and the number of evaluation points (checks, (iii) iterations, restarts) */
+  double ms_gap, ms_kkt, ms_infeas;
+  int64_t evaluations;
 } pdlp_stats;
 
 /* Fills *p with the defaults listed above. */

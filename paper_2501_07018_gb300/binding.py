@@ -93,6 +93,8 @@ class Stats(ctypes.Structure):
         ("polish_pauses", ctypes.c_int64), ("polish_primal_iters", ctypes.c_int64),
         ("polish_dual_iters", ctypes.c_int64), ("polish_accepted_k", ctypes.c_int64),
         ("device_bytes", ctypes.c_int64),
+        ("ms_gap", ctypes.c_double), ("ms_kkt", ctypes.c_double), ("ms_infeas", ctypes.c_double),
+        ("evaluations", ctypes.c_int64),
     ]
 
     def as_dict(self):

@@ -582,6 +582,8 @@ struct Solver {
   GapStats gap_stats;
   int64_t launches = 0;
   double ms_checks = 0.0;
+  double ms_gap = 0.0, ms_kkt = 0.0, ms_infeas = 0.0;
+  int64_t evaluations = 0;
   Clock::time_point t_solve0;
   // feasibility polishing (Algorithm 4)
   T* c_zero = nullptr;                                     // objective of the primal problem
@@ -694,7 +696,9 @@ struct Solver {
     const InfeasMeasures im = infeasibility_measures<T>(in, isc, origv(), P.A, P.AT, g_plain_a,
                                                         g_plain_at, m, n, s, &nl);
     launches += nl;
-    ms_checks += 1e3 * secs_since(t0);
+    const double ms = 1e3 * secs_since(t0);
+    ms_checks += ms;
+    ms_infeas += ms;
     const double eps = prm.eps_infeas;
     const T* ys[3] = {isc.yd, r.b.Y[cur], Ya};
     const T* atys[3] = {isc.atyd, r.b.ATY[cur], ATYa};
@@ -752,7 +756,9 @@ struct Solver {
     const double mu =
         normalized_gap<T>(z, r.X0, r.Y0, omega, vecs(r), gsc, s, &nl, &gap_stats);
     launches += nl;
-    ms_checks += 1e3 * secs_since(t0);
+    const double ms = 1e3 * secs_since(t0);
+    ms_checks += ms;
+    ms_gap += ms;
     return mu;
   }
 
@@ -763,7 +769,9 @@ struct Solver {
     KktSums h;
     PDLP_CUDA_CHECK(cudaMemcpyAsync(&h, kks.out, sizeof(KktSums), cudaMemcpyDeviceToHost, s));
     PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
-    ms_checks += 1e3 * secs_since(t0);
+    const double ms = 1e3 * secs_since(t0);
+    ms_checks += ms;
+    ms_kkt += ms;
     return kkt_finish(h, P.c_norm, P.b_norm);
   }
 
@@ -945,6 +953,7 @@ struct Solver {
       const bool is_art = (double)t >= prm.beta_art * (double)k;
       const bool is_limit = k >= r.max_iters;
       if (!(is_check || is_art || is_limit)) continue;
+      evaluations++;
       // GetRestartCandidate: current vs average since the restart
       launch_average<T>(r.b.Sx, r.b.Sy, r.b.SAx, r.b.SATy, 1.0 / r.hs.W, r.b.lv, r.b.uv, Xa, Ya,
                         AXa, ATYa, m, n, s);
@@ -1290,7 +1299,11 @@ struct Solver {
       st->ms_spmv_a = timer.ms[0];
       st->ms_spmv_at = timer.ms[1];
       st->ms_primal = timer.ms[2];
-      st->ms_checks = ms_checks;
+      st->ms_checks = ms_checks + (aux64 ? aux64->ms_checks : 0.0);
+      st->ms_gap = ms_gap + (aux64 ? aux64->ms_gap : 0.0);
+      st->ms_kkt = ms_kkt + (aux64 ? aux64->ms_kkt : 0.0);
+      st->ms_infeas = ms_infeas + (aux64 ? aux64->ms_infeas : 0.0);
+      st->evaluations = evaluations + (aux64 ? aux64->evaluations : 0);
       st->launches_spmv_a = timer.count[0];
       st->launches_spmv_at = timer.count[1];
       st->kernel_launches = launches + (aux64 ? aux64->launches : 0);
