@@ -107,7 +107,7 @@ class Params:
     """Algorithm constants; defaults are the paper's (Sec. 3 and Sec. 7)."""
 
     eps_rel_kkt: float = 1e-8
-    termination_mode: int = 0  # 0: relative KKT (R10); 1: paper's l_inf + relative gap, Eq. (9)
+    termination_mode: int = 0  # 0: relative KKT (R10); 1: Eq. (9) + Eq. (8); 2: Eq. (10) + Eq. (8)
     eps_abs_feas: float = 1e-8
     eps_rel_gap: float = 1e-2
     max_iters: int = 1_000_000
@@ -502,7 +502,11 @@ def kkt_stats(inst, A_orig, x, y, reduced_costs=0):
     dual residual    (c - A'y) - r                relative: /(1 + ||c||_2)
     pobj = c'x, dobj = lc'y^+ - uc'y^- + lv'r^+ - uv'r^- (Eq. (1) and App. D's expansion)
     gap              |pobj - dobj| / (1 + |pobj| + |dobj|)
-    rel_kkt = max of the three; paper_gap = |pobj - dobj| / (|pobj| + |dobj|) (Eq. (8))."""
+    rel_kkt = max of the three; paper_gap = |pobj - dobj| / (|pobj| + |dobj|) (Eq. (8)).
+    primal_res_rel_inf, dual_res_rel_inf: the l_inf residuals with each row divided by
+    q_i and each column by w_j of Sec. 7's Eq. (10) -- the absolute 1e-8 criterion of
+    Eq. (9) on the paper's rescaled instances, read on the LP as given (see
+    ``row_scale_q``, ``col_scale_w``)."""
     Ax = A_orig @ x
     ATy = A_orig.T @ y
     pres = Ax - proj_box(Ax, inst.lc, inst.uc)
@@ -533,7 +537,26 @@ def kkt_stats(inst, A_orig, x, y, reduced_costs=0):
         rel_gap=eps_g,
         rel_kkt=max(eps_p, eps_d, eps_g),
         paper_gap=paper_gap,
+        primal_res_rel_inf=float(np.max(np.abs(pres) / row_scale_q(inst.lc, inst.uc))) if pres.size else 0.0,
+        dual_res_rel_inf=float(np.max(np.abs(dres) / col_scale_w(inst.c))) if dres.size else 0.0,
     )
+
+
+def row_scale_q(lc, uc):
+    """q_i of Sec. 7's Eq. (10a): the scale of row i's tolerance once the paper's
+    instance rescaling (right-hand sides in {-inf, -1, 0, 1, inf}, Sec. 6) is undone --
+    |lc_i| when only lc_i is finite and nonzero, |uc_i| when only uc_i is, the larger of
+    the two when both are, and 1 when neither is."""
+    lf = np.isfinite(lc) & (lc != 0)
+    uf = np.isfinite(uc) & (uc != 0)
+    with np.errstate(invalid="ignore"):
+        alc, auc = np.abs(np.where(lf, lc, 0.0)), np.abs(np.where(uf, uc, 0.0))
+    return np.where(lf & ~uf, alc, np.where(~lf & uf, auc, np.where(lf & uf, np.maximum(alc, auc), 1.0)))
+
+
+def col_scale_w(c):
+    """w_j of Sec. 7's Eq. (10b): |c_j| when c_j != 0, else 1."""
+    return np.where(c != 0, np.abs(c), 1.0)
 
 
 # ----------------------------------------------------------------------------
@@ -582,10 +605,12 @@ def infeasibility_certificate(inst, A_orig, candidates, eps):
 
 
 def converged(st, prm: Params):
+    """Termination test: 0 relative KKT (R10); 1 the l_inf criteria of Eq. (9) with the
+    relative gap of Eq. (8); 2 the same with Eq. (10)'s scaled residuals (Eq. (9) on the
+    paper's rescaled instance)."""
     if prm.termination_mode == 0:
         return st["rel_kkt"] <= prm.eps_rel_kkt
-    return (st["primal_res_inf"] <= prm.eps_abs_feas and st["dual_res_inf"] <= prm.eps_abs_feas
-            and st["paper_gap"] <= prm.eps_rel_gap)
+    return primal_feasible(st, prm) and dual_feasible(st, prm) and st["paper_gap"] <= prm.eps_rel_gap
 
 
 # ----------------------------------------------------------------------------
@@ -821,6 +846,8 @@ def primal_feasible(st, prm: Params):
     """The primal half of the termination criteria."""
     if prm.termination_mode == 0:
         return st["rel_primal"] <= prm.eps_rel_kkt
+    if prm.termination_mode == 2:
+        return st["primal_res_rel_inf"] <= prm.eps_abs_feas
     return st["primal_res_inf"] <= prm.eps_abs_feas
 
 
@@ -828,6 +855,8 @@ def dual_feasible(st, prm: Params):
     """The dual half of the termination criteria."""
     if prm.termination_mode == 0:
         return st["rel_dual"] <= prm.eps_rel_kkt
+    if prm.termination_mode == 2:
+        return st["dual_res_rel_inf"] <= prm.eps_abs_feas
     return st["dual_res_inf"] <= prm.eps_abs_feas
 
 

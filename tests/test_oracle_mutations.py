@@ -248,3 +248,37 @@ def test_restart_criteria_ii_mistakes_are_caught(monkeypatch, pairs, pin):
     monkeypatch.setattr(O.PdlpRun, "run", _mutated_run_multi(pairs))
     with pytest.raises(AssertionError):
         pin()
+
+
+# --- Eq. (10)'s scaled residuals ------------------------------------------------------
+def _q_max_finite(lc, uc):  # planted: the zero-exclusion of Eq. (10a) dropped
+    lf, uf = np.isfinite(lc), np.isfinite(uc)
+    return np.where(lf | uf, np.maximum(np.where(lf, np.abs(lc), 0.0), np.where(uf, np.abs(uc), 0.0)), 1.0)
+
+
+_row_scale_q = O.row_scale_q
+
+
+def _q_one_when_both(lc, uc):  # planted: two-sided rows given scale 1
+    lf = np.isfinite(lc) & (lc != 0)
+    uf = np.isfinite(uc) & (uc != 0)
+    return np.where(lf & uf, 1.0, _row_scale_q(lc, uc))
+
+
+@pytest.mark.parametrize("bad", [_q_max_finite, _q_one_when_both])
+def test_row_scale_mistakes_are_caught(monkeypatch, bad):
+    monkeypatch.setattr(O, "row_scale_q", bad)
+    with np.errstate(all="ignore"), pytest.raises(AssertionError):
+        P.test_rescaled_criteria_q_and_w_by_hand()
+
+
+def test_scaled_residual_multiplied_is_caught(monkeypatch):
+    orig = O.kkt_stats
+
+    def bad(inst, A, x, y, reduced_costs=0):
+        st = orig(inst, A, x, y, reduced_costs)
+        st["primal_res_rel_inf"] = st["primal_res_inf"]  # the scale not applied
+        return st
+    monkeypatch.setattr(O, "kkt_stats", bad)
+    with pytest.raises(AssertionError):
+        P.test_rescaled_criteria_equal_absolute_residuals_of_the_rescaled_instance()

@@ -716,3 +716,55 @@ def test_app_a_reduced_costs_same_optimum():
     b = O.solve(inst, O.Params(eps_rel_kkt=1e-8, reduced_costs=1))
     assert a.status == b.status == O.OPTIMAL
     assert abs(a.stats["pobj"] - b.stats["pobj"]) <= 1e-6 * abs(a.stats["pobj"])
+
+
+def test_rescaled_criteria_q_and_w_by_hand():
+    """Eq. (10)'s row and column scales on every case of Sec. 7's definition."""
+    inf = math.inf
+    lc = np.array([2.0, -inf, -3.0, -inf, 0.0, 0.0, -4.0, 5.0])
+    uc = np.array([inf, 7.0, 6.0, inf, inf, 8.0, 0.0, 5.0])
+    # only lc finite & nonzero | only uc | both | neither | lc = 0 (not counted), uc inf |
+    # lc = 0, uc | lc, uc = 0 | equality row
+    np.testing.assert_array_equal(O.row_scale_q(lc, uc), [2.0, 7.0, 6.0, 1.0, 1.0, 8.0, 4.0, 5.0])
+    np.testing.assert_array_equal(O.col_scale_w(np.array([-3.0, 0.0, 0.5])), [3.0, 1.0, 0.5])
+
+
+def test_rescaled_criteria_equal_absolute_residuals_of_the_rescaled_instance():
+    """Sec. 7: the absolute l_inf criteria (Eq. (9)) on the paper's rescaled instance
+    (Sec. 6: right-hand sides in {-inf, -1, 0, 1, inf} or scaled to max 1, objective in
+    {-1, 0, 1}) are Eq. (10)'s scaled residuals on the LP as given.  The rescaling is
+    built here explicitly -- row i divided by q_i, column j substituted x'_j = w_j x_j
+    (so c'_j = c_j / w_j), y'_i = q_i y_i -- and kkt_stats of the transformed point on the
+    rescaled LP must give, as absolute residuals, the scaled residuals of the original."""
+    rng = np.random.default_rng(31)
+    inf = math.inf
+    m, n = 12, 9
+    Ad = rng.standard_normal((m, n)) * (rng.random((m, n)) < 0.6)
+    c = rng.choice([-40.0, -2.5, 0.0, 0.3, 7.0, 90.0], n)
+    lc = rng.choice([-inf, 0.0, -3.0, 12.0, 400.0], m)
+    uc = np.where(np.isfinite(lc), lc + rng.choice([0.0, 5.0, inf], m), rng.choice([5.0, 300.0, inf], m))
+    lv = rng.choice([-inf, 0.0, -2.0], n)
+    uv = np.where(np.isfinite(lv), lv + rng.choice([1.0, 20.0, inf], n), rng.choice([4.0, inf], n))
+    inst = H.make_lp(Ad, c, lc, uc, lv, uv)
+    q, w = O.row_scale_q(lc, uc), O.col_scale_w(c)
+    A2 = Ad / q[:, None] / w[None, :]
+    resc = H.make_lp(A2, c / w, lc / q, uc / q, lv * w, uv * w)
+    # the rescaled instance has the form of Sec. 6
+    assert set(np.unique(resc.c)) <= {-1.0, 0.0, 1.0}
+    for a, b in zip(resc.lc, resc.uc):
+        fin = [abs(v) for v in (a, b) if math.isfinite(v) and v != 0]
+        assert not fin or max(fin) == pytest.approx(1.0, rel=1e-15)
+    for _ in range(5):
+        x = rng.standard_normal(n) * 3
+        x = np.clip(x, lv, uv)
+        y = rng.standard_normal(m) * 2
+        y = np.where(~np.isfinite(lc) & (y > 0), -y, y)
+        y = np.where(~np.isfinite(uc) & (y < 0), -y, y)
+        y = np.where(~np.isfinite(lc) & ~np.isfinite(uc), 0.0, y)  # y in Y
+        st = O.kkt_stats(inst, inst.scipy_csr(), x, y)
+        st2 = O.kkt_stats(resc, resc.scipy_csr(), x * w, y * q)
+        assert st["primal_res_rel_inf"] == pytest.approx(st2["primal_res_inf"], rel=1e-13, abs=1e-15)
+        assert st["dual_res_rel_inf"] == pytest.approx(st2["dual_res_inf"], rel=1e-13, abs=1e-15)
+        # objectives and the relative gap of Eq. (8) are unchanged by the rescaling
+        assert st["pobj"] == pytest.approx(st2["pobj"], rel=1e-13)
+        assert st["paper_gap"] == pytest.approx(st2["paper_gap"], rel=1e-12, abs=1e-15)
