@@ -71,7 +71,14 @@ typedef struct {
                               <= this.  Default 1e-8.                               */
   int termination_mode;    /* 0: relative KKT; 1: Sec. 7 / Eq. (9): l_inf primal and
                               dual residual <= eps_abs_feas and the relative gap of
-                              Eq. (8) <= eps_rel_gap.                               */
+                              Eq. (8) <= eps_rel_gap; 2: the same on the paper's
+                              rescaled instances (Sec. 6: right-hand sides and costs
+                              scaled to magnitude 1), read on the LP as given (Eq.
+                              (10)): row i's violation <= eps_abs_feas q_i with q_i the
+                              largest magnitude of its finite nonzero bounds (1 if
+                              none), column j's dual residual <= eps_abs_feas |c_j|
+                              (eps_abs_feas if c_j = 0).  Polishing phases use the
+                              primal / dual half of the criteria in force.          */
   double eps_abs_feas;     /* default 1e-8                                          */
   double eps_rel_gap;      /* default 1e-2                                          */
   int64_t max_iters;       /* accepted PDHG iterations; default 1e9                  */
@@ -180,6 +187,9 @@ typedef struct {
      tests, and the number of evaluation points (checks, (iii) iterations, restarts) */
   double ms_gap, ms_kkt, ms_infeas;
   int64_t evaluations;
+  /* l_inf residuals of the returned point with row i divided by q_i and column j by
+     w_j of Sec. 7's Eq. (10) (see termination_mode 2) */
+  double primal_res_rel_inf, dual_res_rel_inf;
 } pdlp_stats;
 
 /* Fills *p with the defaults listed above. */

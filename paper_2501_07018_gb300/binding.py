@@ -95,6 +95,7 @@ class Stats(ctypes.Structure):
         ("device_bytes", ctypes.c_int64),
         ("ms_gap", ctypes.c_double), ("ms_kkt", ctypes.c_double), ("ms_infeas", ctypes.c_double),
         ("evaluations", ctypes.c_int64),
+        ("primal_res_rel_inf", ctypes.c_double), ("dual_res_rel_inf", ctypes.c_double),
     ]
 
     def as_dict(self):

@@ -40,13 +40,18 @@ __global__ void __launch_bounds__(kThreads)
     k_kkt(PointRef<T> z, OrigVecs o, int64_t m, int64_t n, KktScratch ks, int rc_mode) {
   __shared__ double red[5 * kWarps];
   double v[5] = {0, 0, 0, 0, 0};  // pres2, dres2, pobj, dobj_rows, dobj_cols
-  double mx[2] = {0, 0};
+  double mx[4] = {0, 0, 0, 0};     // l_inf residuals, then scaled by Eq. (10)'s q_i, w_j
   for (int64_t i = gi(); i < m; i += gs()) {
     const double ax = (double)z.ax[i] * o.inv_d1[i];
     const double y = (double)z.y[i] * o.d1[i];
-    const double pr = ax - fmin(fmax(ax, o.lc[i]), o.uc[i]);
+    const double lc = o.lc[i], uc = o.uc[i];
+    const double pr = ax - fmin(fmax(ax, lc), uc);
     v[0] += pr * pr;
     mx[0] = fmax(mx[0], fabs(pr));
+    // q_i (Sec. 7, Eq. (10a)): the finite nonzero bounds' largest magnitude, else 1
+    const bool lq = isfinite(lc) && lc != 0.0, uq = isfinite(uc) && uc != 0.0;
+    const double q = lq ? (uq ? fmax(fabs(lc), fabs(uc)) : fabs(lc)) : (uq ? fabs(uc) : 1.0);
+    mx[2] = fmax(mx[2], fabs(pr) / q);
     if (y > 0.0)
       v[3] += o.lc[i] * y;
     else if (y < 0.0)
@@ -71,6 +76,7 @@ __global__ void __launch_bounds__(kThreads)
     const double dr = g - r;
     v[1] += dr * dr;
     mx[1] = fmax(mx[1], fabs(dr));
+    mx[3] = fmax(mx[3], fabs(dr) / (o.c[j] != 0.0 ? fabs(o.c[j]) : 1.0));  // w_j, Eq. (10b)
     v[2] += o.c[j] * x;
     if (r > 0.0)
       v[4] += o.lv[j] * r;
@@ -79,38 +85,36 @@ __global__ void __launch_bounds__(kThreads)
   }
   block_sum<5>(v, red);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  mx[0] = warp_max(mx[0]);
-  mx[1] = warp_max(mx[1]);
-  __shared__ double mred[2 * kWarps];
-  if (lane == 0) {
-    mred[warp] = mx[0];
-    mred[kWarps + warp] = mx[1];
+  __shared__ double mred[4 * kWarps];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double t = warp_max(mx[k]);
+    if (lane == 0) mred[k * kWarps + warp] = t;
   }
   __syncthreads();
   const int G = gridDim.x;
   if (threadIdx.x == 0) {
-    double a = 0, b = 0;
-    for (int w = 0; w < kWarps; ++w) {
-      a = fmax(a, mred[w]);
-      b = fmax(b, mred[kWarps + w]);
-    }
     for (int k = 0; k < 5; ++k) ks.part[k * G + blockIdx.x] = v[k];
-    ks.part[5 * G + blockIdx.x] = a;
-    ks.part[6 * G + blockIdx.x] = b;
+    for (int k = 0; k < 4; ++k) {
+      double a = 0;
+      for (int w = 0; w < kWarps; ++w) a = fmax(a, mred[k * kWarps + w]);
+      ks.part[(5 + k) * G + blockIdx.x] = a;
+    }
   }
   if (!last_block_arrival(ks.counter)) return;
-  double tot[5], mxt[2];
-  block_reduce_partials<5, 2>(ks.part, G, tot, mxt, red, mred);
+  double tot[5], mxt[4];
+  block_reduce_partials<5, 4>(ks.part, G, tot, mxt, red, mred);
   if (threadIdx.x == 0) {
-    const double a = mxt[0], b = mxt[1];
     KktSums r;
     r.pres2 = tot[0];
     r.dres2 = tot[1];
     r.pobj = tot[2];
     r.dobj_rows = tot[3];
     r.dobj_cols = tot[4];
-    r.pres_max = a;
-    r.dres_max = b;
+    r.pres_max = mxt[0];
+    r.dres_max = mxt[1];
+    r.pres_rel_max = mxt[2];
+    r.dres_rel_max = mxt[3];
     *ks.out = r;
   }
 }

@@ -44,11 +44,12 @@ struct OrigVecs {
 // KKT sums of a point (unscaled LP); see kkt_finish in solver.cu for their use.
 struct KktSums {
   double pres2, dres2, pres_max, dres_max, pobj, dobj_rows, dobj_cols;
+  double pres_rel_max, dres_rel_max;  // l_inf residuals scaled as in Sec. 7's Eq. (10)
 };
 
 // Scratch of the KKT reduction (partials, counter, result), sized for grid_ctas(4).
 struct KktScratch {
-  double* part;  // [7 * grid]
+  double* part;  // [9 * grid]
   unsigned int* counter;
   KktSums* out;
   int grid;

@@ -434,6 +434,7 @@ static void build_problem(DeviceArena& arena, const Inputs& in, const DevInputs&
 struct KktResult {
   double rel_kkt, rel_primal, rel_dual, rel_gap, pres2, dres2, pres_inf, dres_inf, pobj, dobj,
       paper_gap;
+  double pres_rel_inf, dres_rel_inf;  // Sec. 7, Eq. (10)
 };
 
 static KktResult kkt_finish(const KktSums& k, double c_norm, double b_norm) {
@@ -442,6 +443,8 @@ static KktResult kkt_finish(const KktSums& k, double c_norm, double b_norm) {
   r.dres2 = std::sqrt(k.dres2);
   r.pres_inf = k.pres_max;
   r.dres_inf = k.dres_max;
+  r.pres_rel_inf = k.pres_rel_max;
+  r.dres_rel_inf = k.dres_rel_max;
   r.pobj = k.pobj;
   r.dobj = k.dobj_rows + k.dobj_cols;
   r.rel_primal = r.pres2 / (1.0 + b_norm);
@@ -453,9 +456,20 @@ static KktResult kkt_finish(const KktSums& k, double c_norm, double b_norm) {
   return r;
 }
 
+// the primal / dual halves of the termination criteria: relative KKT (mode 0), the l_inf
+// residuals of Eq. (9) (mode 1), or those residuals scaled as in Eq. (10) (mode 2)
+static bool primal_ok(const KktResult& r, const pdlp_params& p) {
+  if (p.termination_mode == 0) return r.rel_primal <= p.eps_rel_kkt;
+  return (p.termination_mode == 2 ? r.pres_rel_inf : r.pres_inf) <= p.eps_abs_feas;
+}
+static bool dual_ok(const KktResult& r, const pdlp_params& p) {
+  if (p.termination_mode == 0) return r.rel_dual <= p.eps_rel_kkt;
+  return (p.termination_mode == 2 ? r.dres_rel_inf : r.dres_inf) <= p.eps_abs_feas;
+}
+
 static bool converged(const KktResult& r, const pdlp_params& p) {
   if (p.termination_mode == 0) return r.rel_kkt <= p.eps_rel_kkt;
-  return r.pres_inf <= p.eps_abs_feas && r.dres_inf <= p.eps_abs_feas && r.paper_gap <= p.eps_rel_gap;
+  return primal_ok(r, p) && dual_ok(r, p) && r.paper_gap <= p.eps_rel_gap;
 }
 
 using Clock = std::chrono::steady_clock;
@@ -509,10 +523,8 @@ struct EventTimer {
 enum Goal { kGoalOptimal = 0, kGoalPrimalFeasible = 1, kGoalDualFeasible = 2 };
 
 static bool goal_met(const KktResult& r, const pdlp_params& p, int goal) {
-  if (goal == kGoalPrimalFeasible)
-    return p.termination_mode == 0 ? r.rel_primal <= p.eps_rel_kkt : r.pres_inf <= p.eps_abs_feas;
-  if (goal == kGoalDualFeasible)
-    return p.termination_mode == 0 ? r.rel_dual <= p.eps_rel_kkt : r.dres_inf <= p.eps_abs_feas;
+  if (goal == kGoalPrimalFeasible) return primal_ok(r, p);
+  if (goal == kGoalDualFeasible) return dual_ok(r, p);
   return converged(r, p);
 }
 
@@ -613,7 +625,7 @@ struct Solver {
     PDLP_CUDA_CHECK(cudaMemsetAsync(counters, 0, 8 * sizeof(unsigned int), s));
     kks.grid = g_red;
     kks.rc_mode = prm.reduced_costs;
-    kks.part = arena.alloc<double>(7 * (int64_t)g_red);
+    kks.part = arena.alloc<double>(9 * (int64_t)g_red);
     kks.counter = counters + 1;
     kks.out = arena.alloc<KktSums>(1);
     gsc.grid = g_red;
@@ -971,8 +983,12 @@ struct Solver {
       if (is_check || is_limit) {
         out_k = kkt(cand);
         if (prm.verbose)
-          std::fprintf(stderr, "pdlp: goal=%d k=%lld rel_kkt=%.3e pobj=%.10e omega=%.3e eta=%.3e\n",
-                       r.goal, (long long)k, out_k.rel_kkt, out_k.pobj, omega, r.hs.eta_hat);
+          std::fprintf(stderr,
+                       "pdlp: goal=%d k=%lld rel_kkt=%.3e pres_inf=%.3e dres_inf=%.3e gap8=%.3e "
+                       "pobj=%.10e omega=%.3e eta=%.3e restarts=%lld/%lld/%lld\n",
+                       r.goal, (long long)k, out_k.rel_kkt, out_k.pres_inf, out_k.dres_inf,
+                       out_k.paper_gap, out_k.pobj, omega, r.hs.eta_hat, (long long)r.restarts[0],
+                       (long long)r.restarts[1], (long long)r.restarts[2]);
         if (goal_met(out_k, prm, r.goal)) {
           out_pt = cand;
           return kRunDone;
@@ -1162,6 +1178,9 @@ struct Solver {
         row[1] = kz.paper_gap;
       }
       pol.pauses++;
+      if (prm.verbose)
+        std::fprintf(stderr, "pdlp: pause k=%lld average: gap8=%.3e pres_inf=%.3e dres_inf=%.3e\n",
+                     (long long)kp, kz.paper_gap, kz.pres_inf, kz.dres_inf);
       if (!(kz.paper_gap < prm.eps_rel_gap)) continue;
       const double omega = main_run.hs.omega, eta = main_run.hs.eta_hat;
       const int64_t budget = kp / 8;
@@ -1299,6 +1318,8 @@ struct Solver {
       st->ms_spmv_a = timer.ms[0];
       st->ms_spmv_at = timer.ms[1];
       st->ms_primal = timer.ms[2];
+      st->primal_res_rel_inf = out_k.pres_rel_inf;
+      st->dual_res_rel_inf = out_k.dres_rel_inf;
       st->ms_checks = ms_checks + (aux64 ? aux64->ms_checks : 0.0);
       st->ms_gap = ms_gap + (aux64 ? aux64->ms_gap : 0.0);
       st->ms_kkt = ms_kkt + (aux64 ? aux64->ms_kkt : 0.0);
@@ -1500,6 +1521,8 @@ int pdlp_solve(int64_t m, int64_t n, const pdlp_csr* A, const double* c, const d
     if (prm.pc_alpha >= 2.0) throw PdlpError(-1, "pc_alpha must be < 2");
     if (prm.max_iters < 1 || prm.check_period < 1 || prm.max_step_retries < 1)
       throw PdlpError(-1, "max_iters, check_period and max_step_retries must be >= 1");
+    if (prm.termination_mode < 0 || prm.termination_mode > 2)
+      throw PdlpError(-1, "termination_mode must be 0, 1 or 2");
     if (!(prm.beta_art >= 0.0) || std::isnan(prm.beta_suff) || std::isnan(prm.beta_nec))
       throw PdlpError(-1, "beta_art must be >= 0 (>= 1: criterion (iii) off); beta_suff and beta_nec not NaN");
     if (!(prm.fixed_step >= 0.0 && std::isfinite(prm.fixed_step)) ||
