@@ -75,6 +75,11 @@ used):
       R1's start, with the dual step of R17/R18; at a clamp boundary (u = lv, yh =
       -sigma uc, ...) the derivative of the inside branch is taken as 0 for the
       iterate (measure-zero set).
+  R25 The paper's experiments stop at absolute l_inf residuals of 1e-8 on instances
+      rescaled first (Sec. 6: right-hand sides and costs of magnitude 1); on the LP as
+      given that is Eq. (10) (row tolerance 1e-8 q_i, column tolerance 1e-8 w_j).
+      ``termination_mode`` 2 applies it to instances that were not rescaled; mode 1 is
+      the absolute criterion as written.
 
 Pins (tests/): closed forms, brute force, HiGHS, finite differences and hand-solved LPs
 for every function.  The restart decisions of ``PdlpRun`` are pinned by closed-form
