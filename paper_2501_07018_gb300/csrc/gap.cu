@@ -93,6 +93,7 @@ __global__ void __launch_bounds__(kThreads)
   }
   __syncthreads();
   const int G = gridDim.x;
+  static_assert(kKktPartials == 5 + 4, "KKT partial arrays");
   if (threadIdx.x == 0) {
     for (int k = 0; k < 5; ++k) ks.part[k * G + blockIdx.x] = v[k];
     for (int k = 0; k < 4; ++k) {

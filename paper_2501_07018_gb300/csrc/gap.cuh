@@ -48,8 +48,9 @@ struct KktSums {
 };
 
 // Scratch of the KKT reduction (partials, counter, result), sized for grid_ctas(4).
+constexpr int kKktPartials = 9;  // 5 sums and 4 maxima per CTA
 struct KktScratch {
-  double* part;  // [9 * grid]
+  double* part;  // [kKktPartials * grid]
   unsigned int* counter;
   KktSums* out;
   int grid;

@@ -625,7 +625,7 @@ struct Solver {
     PDLP_CUDA_CHECK(cudaMemsetAsync(counters, 0, 8 * sizeof(unsigned int), s));
     kks.grid = g_red;
     kks.rc_mode = prm.reduced_costs;
-    kks.part = arena.alloc<double>(9 * (int64_t)g_red);
+    kks.part = arena.alloc<double>(kKktPartials * (int64_t)g_red);
     kks.counter = counters + 1;
     kks.out = arena.alloc<KktSums>(1);
     gsc.grid = g_red;
@@ -984,10 +984,12 @@ struct Solver {
         out_k = kkt(cand);
         if (prm.verbose)
           std::fprintf(stderr,
-                       "pdlp: goal=%d k=%lld rel_kkt=%.3e pres_inf=%.3e dres_inf=%.3e gap8=%.3e "
-                       "pobj=%.10e omega=%.3e eta=%.3e restarts=%lld/%lld/%lld\n",
+                       "pdlp: goal=%d k=%lld rel_kkt=%.3e pres_inf=%.3e dres_inf=%.3e "
+                       "pres_eq10=%.3e dres_eq10=%.3e gap8=%.3e pobj=%.10e omega=%.3e eta=%.3e "
+                       "restarts=%lld/%lld/%lld\n",
                        r.goal, (long long)k, out_k.rel_kkt, out_k.pres_inf, out_k.dres_inf,
-                       out_k.paper_gap, out_k.pobj, omega, r.hs.eta_hat, (long long)r.restarts[0],
+                       out_k.pres_rel_inf, out_k.dres_rel_inf, out_k.paper_gap, out_k.pobj, omega,
+                       r.hs.eta_hat, (long long)r.restarts[0],
                        (long long)r.restarts[1], (long long)r.restarts[2]);
         if (goal_met(out_k, prm, r.goal)) {
           out_pt = cand;
@@ -1807,7 +1809,7 @@ int pdlp_kkt(int64_t m, int64_t n, const pdlp_csr* A, const double* c, const dou
     KktScratch ks;
     ks.grid = g;
     ks.rc_mode = prm.reduced_costs;
-    ks.part = pp.arena.alloc<double>(7 * (int64_t)g);
+    ks.part = pp.arena.alloc<double>(kKktPartials * (int64_t)g);
     ks.counter = pp.arena.alloc<unsigned int>(1);
     ks.out = pp.arena.alloc<KktSums>(1);
     PDLP_CUDA_CHECK(cudaMemsetAsync(ks.counter, 0, sizeof(unsigned int), sg.s));
