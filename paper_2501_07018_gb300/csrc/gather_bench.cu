@@ -24,6 +24,7 @@
 
 #include "pdlp.h"
 #include "problem.cuh"
+#include "tma.cuh"
 
 namespace pdlp {
 namespace {
@@ -105,31 +106,10 @@ __device__ __forceinline__ T gb_slice_lsu(const int32_t* __restrict__ cp, const 
   return acc;
 }
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
 // Waits for the phase with the given parity; gives up after kSpinLimit polls (error
 // flag set), then polls as long again so that copies in flight land before the buffer
 // is reused or the CTA exits.
-__device__ __forceinline__ void mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err) {
+__device__ __forceinline__ void gb_wait(uint64_t* bar, uint32_t parity, int* err) {
   uint32_t spins = 0;
   while (!mbar_try_wait(bar, parity)) {
     if (++spins > kSpinLimit) {
@@ -175,7 +155,7 @@ __device__ __forceinline__ double gb_slice_tma(const int32_t* __restrict__ cp,
     }
     if (st < 0) continue;
     const int b = st & 1;
-    mbar_wait_bounded(&bars[b], b ? ph1 : ph0, err);
+    gb_wait(&bars[b], b ? ph1 : ph0, err);
     if (b)
       ph1 ^= 1u;
     else
