@@ -601,30 +601,61 @@ def polishing_mcf(pkg, scale=0.1, plain_limit_s=30.0):
     return res
 
 
-def batch_uneven(pkg, count=128, concurrency=16):
-    """pdlp_solve_batch on ``count`` LPs of the uneven-size batch (m ~ U{500..20000},
-    n ~ U{1.5m..3m}, 4-12 entries per column), FP64, each to relative KKT 1e-6: wall
-    clock with host arrays, LPs/s and the iterations of all LPs per second."""
+def batch_uneven(pkg, count=1024, pool_count=128, concurrency=16):
+    """The uneven batch as configured: ``count`` LPs (m ~ U{500..20000}, n ~ U{1.5m..3m},
+    4-12 N(0,1) entries per column), each solved to relative KKT 1e-6 in ONE persistent
+    launch (pdlp_solve_batch_persistent; its autotuner picks the launch configuration),
+    FP32 bulk with FP64 checks and, for comparison, FP64; host arrays.  Reports the wall
+    clock of the call (setup, autotuning, launch, copies), LPs/s, the launch's device
+    time, LP-iterations per second of the launch, and the launch's algorithmic bytes --
+    per LP, its iterations times the bytes of one iteration (both products with 4-byte
+    indices, the vectors: 2 nnz (v + 4) + 8 (m + n + 2) + 11 (m + n) v) -- per second
+    against the measured HBM bandwidth.  The stream pool (pdlp_solve_batch,
+    ``concurrency`` LPs in flight, FP64) runs the first ``pool_count`` LPs."""
     import lpgen
 
     insts = lpgen.config2(count)
     nnz = sum(i.nnz for i in insts)
+    peak = measured_peaks()
+    hbm = peak.get("hbm_gbs") if peak else None
     res = {"workload": f"{count} LPs of uneven size (sum nnz {nnz}), relative KKT 1e-6, "
-                       f"{concurrency} in flight, host arrays"}
-    # FP64 only: FP32 iterates barely resolve relative KKT 1e-6 (several times the
-    # iterations, some LPs at the limit), which would make this leg take minutes
-    for name, prec in (("fp64", pkg.FP64),):
+                       f"one persistent launch, host arrays"}
+    for name, prec in (("fp32_bulk", pkg.FP32_BULK), ("fp64", pkg.FP64)):
+        v = 4 if prec == pkg.FP32_BULK else 8
         t0 = time.perf_counter()
-        got = pkg.solve_batch(insts, concurrency=concurrency, precision=prec, eps_rel_kkt=1e-6,
-                              max_iters=200000, time_limit_s=120.0)
+        got = pkg.solve_batch(insts, persistent=True, tune=0, precision=prec, eps_rel_kkt=1e-6,
+                              max_iters=400000, time_limit_s=120.0)
         wall = time.perf_counter() - t0
         its = sum(r.stats["iterations"] for r in got)
+        launch = got[0].stats["batch_launch_s"]
+        alg = sum(r.stats["iterations"] * (2.0 * i.nnz * (v + 4) + 8.0 * (i.m + i.n + 2)
+                                           + 11.0 * (i.m + i.n) * v) for i, r in zip(insts, got))
         st = {}
         for r in got:
             st[r.status_name] = st.get(r.status_name, 0) + 1
-        res[name] = {"seconds": wall, "lps_per_s": count / wall, "iters_per_s": its / wall,
-                     "iterations_total": its, "statuses": st,
-                     "max_rel_kkt": max(r.stats["rel_kkt"] for r in got)}
+        ph = [sum(r.stats[k] for r in got) for k in ("ms_primal", "ms_spmv_a", "ms_spmv_at",
+                                                       "ms_checks")]
+        tot = sum(ph) or 1.0
+        achieved = alg / launch / 1e9 if launch > 0 else None
+        res[name] = {"seconds": wall, "launch_s": launch, "lps_per_s": count / wall,
+                     "lp_iters_per_s_launch": its / launch if launch > 0 else None,
+                     "iterations_total": its,
+                     "iterations_max": max(r.stats["iterations"] for r in got),
+                     "statuses": st, "max_rel_kkt": max(r.stats["rel_kkt"] for r in got),
+                     "config": got[0].stats["tune"],
+                     "phase_share": {k: round(x / tot, 3) for k, x in
+                                     zip(("primal", "spmv_a_dual", "spmv_at_sums", "checks"), ph)},
+                     "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm,
+                                  "unit": "GB/s", "frac": achieved / hbm if achieved and hbm else None,
+                                  "algorithmic_bytes": alg}}
+    pool = insts[:pool_count]
+    t0 = time.perf_counter()
+    got = pkg.solve_batch(pool, concurrency=concurrency, precision=pkg.FP64, eps_rel_kkt=1e-6,
+                          max_iters=200000, time_limit_s=120.0)
+    wall = time.perf_counter() - t0
+    res["stream_pool_fp64"] = {"lps": pool_count, "seconds": wall, "lps_per_s": pool_count / wall,
+                               "iterations_total": sum(r.stats["iterations"] for r in got),
+                               "optimal": sum(1 for r in got if r.status == 0)}
     return res
 
 

@@ -190,6 +190,10 @@ typedef struct {
   /* l_inf residuals of the returned point with row i divided by q_i and column j by
      w_j of Sec. 7's Eq. (10) (see termination_mode 2) */
   double primal_res_rel_inf, dual_res_rel_inf;
+  /* pdlp_solve_batch_persistent: device time of the whole persistent launch (CUDA
+     events; the same for every LP of the call), and the SM that solved this LP */
+  double batch_launch_s;
+  int64_t batch_sm;
 } pdlp_stats;
 
 /* Fills *p with the defaults listed above. */
@@ -286,6 +290,36 @@ typedef struct {
  * negative code), PDLP_INVALID_ARGUMENT for bad arguments of the call itself. */
 int pdlp_solve_batch(int64_t count, const pdlp_problem* problems, const pdlp_params* p,
                      int concurrency, int* status_out, pdlp_stats* stats_out);
+
+/* The batch of pdlp_solve_batch solved by ONE persistent kernel launch: each CTA takes
+ * LPs from a device queue, largest first, and runs the whole method on its LP alone --
+ * Algorithm 1 with the adaptive steps of Algorithm 2, the restart scheme of Sec. 3,
+ * Algorithm 3's primal weight and App. C's infeasibility tests, each LP with its own
+ * step sizes, primal weight, restarts and termination (the same rules as pdlp_solve,
+ * with its own reduction order, so iterates agree with pdlp_solve's to rounding, not
+ * bit for bit; one run is deterministic for a fixed `tune`).  The setup of Sec. 3
+ * (preconditioning, layouts) runs per LP on 16 worker streams first.  The vectors the
+ * two sparse products gather are held in shared memory when an LP's fit (x' and y',
+ * else the one that fits, x' first).
+ *   tune: 0 = autotune -- time 128 iterations of a sample of the batch (spread over
+ *   its sizes) under every launch configuration and solve with the fastest; 1..6 = that
+ *   configuration (threads per CTA / CTAs per SM / shared memory per CTA / staging):
+ *   1 = 1024/1/200 KB/on, 2 = 1024/1/200 KB/off, 3 = 768/1/200 KB/on, 4 = 512/1/200 KB/on,
+ *   5 = 512/2/100 KB/on, 6 = 512/2/100 KB/off.  tune_out (may be NULL) receives the
+ *   configuration used.
+ *   params: as pdlp_solve_batch; feasibility_polishing must be 0; trace, polish log,
+ *   profile and verbose are ignored.  precision PDLP_FP32_BULK keeps FP64 for the KKT
+ *   measures, the normalized gaps, the restart decisions and the primal weight.
+ *   status_out[count], stats_out[count] (may be NULL) as pdlp_solve_batch; in stats,
+ *   seconds_solve is the LP's device time inside the launch, seconds_setup its setup,
+ *   seconds_total the whole call; ms_primal, ms_spmv_a, ms_spmv_at and ms_checks split
+ *   seconds_solve by phase (the primal step; A x' with the dual step and Algorithm 2;
+ *   A'y' with the running sums; evaluation points, start and output), in proportion
+ *   to the SM clock cycles the CTA spent in each.
+ * Returns 0 when every LP was attempted (see status_out), or a negative code for bad
+ * arguments of the call itself. */
+int pdlp_solve_batch_persistent(int64_t count, const pdlp_problem* problems, const pdlp_params* p,
+                                int tune, int* status_out, pdlp_stats* stats_out, int* tune_out);
 
 /* Unrolled PDHG and its adjoint (a differentiable layer; Eq. (3), Sec. 2): K steps of
  * Eq. (3) on the LP as given -- no preconditioning, restarts or adaptive steps: the

@@ -96,6 +96,7 @@ class Stats(ctypes.Structure):
         ("ms_gap", ctypes.c_double), ("ms_kkt", ctypes.c_double), ("ms_infeas", ctypes.c_double),
         ("evaluations", ctypes.c_int64),
         ("primal_res_rel_inf", ctypes.c_double), ("dual_res_rel_inf", ctypes.c_double),
+        ("batch_launch_s", ctypes.c_double), ("batch_sm", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -143,6 +144,9 @@ def load_library(path: str | None = None):
     lib.pdlp_kkt_products_noalloc.restype = ctypes.c_int
     lib.pdlp_solve_batch.argtypes = [i64, P, ctypes.POINTER(Params), ctypes.c_int, P, P]
     lib.pdlp_solve_batch.restype = ctypes.c_int
+    lib.pdlp_solve_batch_persistent.argtypes = [i64, P, ctypes.POINTER(Params), ctypes.c_int, P,
+                                                P, P]
+    lib.pdlp_solve_batch_persistent.restype = ctypes.c_int
     lib.pdlp_unrolled_pdhg.argtypes = [i64, i64, ctypes.POINTER(Csr), P, P, P, P, P, i64,
                                        ctypes.c_double, ctypes.c_double, i64, P, P,
                                        ctypes.POINTER(Params), P, P, P, P, P, P, P]
@@ -316,11 +320,15 @@ def solve_instance(inst, trace_iters: int = 0, device: bool = False, **params) -
     return solve(inst.m, inst.n, *arrs, trace_iters=trace_iters, **params)
 
 
-def solve_batch(instances, device: bool = False, concurrency: int = 16, **params) -> list:
+def solve_batch(instances, device: bool = False, concurrency: int = 16, persistent: bool = False,
+                tune: int = 0, **params) -> list:
     """pdlp_solve_batch over objects with m, n, row_ptr, col_idx, val, c, lc, uc, lv, uv
     attributes (host arrays; ``device=True`` stages them as CUDA tensors first).
-    Returns one SolveResult per instance, in order; a negative status does not raise
-    (its message is in ``stats['error']`` of the first failing instance)."""
+    ``persistent=True`` calls pdlp_solve_batch_persistent instead (one launch for the
+    whole batch; ``tune`` as there, the configuration used lands in every result's
+    ``stats['tune']``).  Returns one SolveResult per instance, in order; a negative
+    status does not raise (its message is in ``stats['error']`` of the first failing
+    instance)."""
     lib = load_library()
     mh = _Marshal(device)
     probs = (Problem * max(1, len(instances)))()
@@ -342,12 +350,22 @@ def solve_batch(instances, device: bool = False, concurrency: int = 16, **params
     prm = _params_for(device, params)
     status = (ctypes.c_int * max(1, len(instances)))()
     stats = (Stats * max(1, len(instances)))()
-    _check(lib.pdlp_solve_batch(len(instances), ctypes.addressof(probs), ctypes.byref(prm),
-                                int(concurrency), ctypes.addressof(status), ctypes.addressof(stats)))
+    tune_used = ctypes.c_int(0)
+    if persistent:
+        _check(lib.pdlp_solve_batch_persistent(len(instances), ctypes.addressof(probs),
+                                               ctypes.byref(prm), int(tune),
+                                               ctypes.addressof(status), ctypes.addressof(stats),
+                                               ctypes.addressof(tune_used)))
+    else:
+        _check(lib.pdlp_solve_batch(len(instances), ctypes.addressof(probs), ctypes.byref(prm),
+                                    int(concurrency), ctypes.addressof(status),
+                                    ctypes.addressof(stats)))
     res = []
     first_error = lib.pdlp_last_error().decode()
     for k, (x, y) in enumerate(outs):
         st = stats[k].as_dict()
+        if persistent:
+            st["tune"] = tune_used.value
         if status[k] < 0 and first_error:
             st["error"] = first_error
             first_error = ""

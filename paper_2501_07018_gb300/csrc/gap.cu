@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "gap.cuh"
+#include "gap_paths.cuh"
 
 namespace pdlp {
 
@@ -215,113 +216,6 @@ struct GapCtx {
 size_t gap_ctx_bytes() { return sizeof(GapCtx); }
 size_t gap_param_bytes(int64_t m, int64_t n) {
   return sizeof(float4) * (size_t)m + 3 * sizeof(float) * (size_t)n + 256;
-}
-
-// Path of one column: g = c - A'y; it moves toward lv (g > 0) or uv (g < 0) at rate
-// |g| / omega per unit s and parks after travelling `room`.
-struct XPath {
-  double g, ga, room;
-  bool moves;
-};
-__device__ __forceinline__ XPath x_path(double x, double c, double aty, double lv, double uv) {
-  XPath p;
-  p.g = c - aty;
-  p.ga = fabs(p.g);
-  p.moves = p.g != 0.0;
-  p.room = p.g > 0.0 ? x - lv : (p.g < 0.0 ? uv - x : 0.0);
-  return p;
-}
-
-// Path of one row (kind 0: fixed; 1: moves away forever with slope k1; 2: moves to 0
-// with slope k1 and parks; 3: moves to 0, parks, then moves on with slope k2).
-struct YPath {
-  double y, k1, k2;
-  int kind;
-};
-__device__ __forceinline__ YPath y_path(double y, double lc, double uc, double ax) {
-  YPath p;
-  p.y = y;
-  p.k1 = 0.0;
-  p.k2 = 0.0;
-  p.kind = 0;
-  const bool lf = isfinite(lc), uf = isfinite(uc);
-  const double a = lc - ax, b = uc - ax;
-  if (y > 0.0) {
-    if (a > 0.0) {
-      p.kind = 1;
-      p.k1 = a;
-    } else if (a < 0.0) {
-      p.k1 = a;
-      if (uf && b < 0.0) {
-        p.kind = 3;
-        p.k2 = b;
-      } else {
-        p.kind = 2;
-      }
-    }
-  } else if (y < 0.0) {
-    if (b < 0.0) {
-      p.kind = 1;
-      p.k1 = b;
-    } else if (b > 0.0) {
-      p.k1 = b;
-      if (lf && a > 0.0) {
-        p.kind = 3;
-        p.k2 = a;
-      } else {
-        p.kind = 2;
-      }
-    }
-  } else {
-    if (lf && a > 0.0) {
-      p.kind = 1;
-      p.k1 = a;
-    } else if (uf && b < 0.0) {
-      p.kind = 1;
-      p.k1 = b;
-    }
-  }
-  return p;
-}
-
-// Coefficients (alpha, gamma, beta, phi) of a column / row at s.
-__device__ __forceinline__ void x_coef(const XPath& p, double s, double om, double iom,
-                                       double* c4) {
-  if (!p.moves) return;
-  if (s * p.ga < om * p.room) {
-    const double w = p.g * p.g * iom;
-    c4[0] += w;
-    c4[2] += w;
-  } else {
-    c4[1] += om * p.room * p.room;
-    c4[3] += p.ga * p.room;
-  }
-}
-__device__ __forceinline__ int y_piece(const YPath& p, double s, double om) {
-  // 1 moving (first piece), 2 parked at 0, 3 moving again
-  if (p.kind == 1) return 1;
-  const double ay = fabs(p.y);
-  if (s * (om * fabs(p.k1)) < ay) return 1;
-  if (p.kind == 3 && s * (om * fabs(p.k2)) >= ay) return 3;
-  return 2;
-}
-__device__ __forceinline__ void y_coef(const YPath& p, double s, double om, double iom,
-                                       double* c4) {
-  if (p.kind == 0) return;
-  const int pc = y_piece(p, s, om);
-  if (pc == 1) {
-    const double w = om * p.k1 * p.k1;
-    c4[0] += w;
-    c4[2] += w;
-  } else if (pc == 2) {
-    c4[1] += p.y * p.y * iom;
-    c4[3] += -p.k1 * p.y;
-  } else {
-    const double w = om * p.k2 * p.k2;
-    c4[0] += w;
-    c4[2] += w;
-    c4[3] += (p.k2 - p.k1) * p.y;
-  }
 }
 
 // FP32 parameters of the bracket scan, written by pass 0: per column
@@ -684,34 +578,10 @@ template <class T>
 __device__ void cand_info(const GapArgs<T>& a, double om, int64_t code, double* bp, double* d4) {
   const int64_t idx = code >> 2;
   const int which = (int)(code & 3);
-  d4[0] = d4[1] = d4[2] = d4[3] = 0.0;
-  if (which == 0) {
-    const XPath q = x_path(a.z.x[idx], a.p.c[idx], a.z.aty[idx], a.p.lv[idx], a.p.uv[idx]);
-    *bp = om * q.room / q.ga;
-    const double w = q.g * q.g * (1.0 / om);
-    d4[0] = -w;
-    d4[1] = om * q.room * q.room;
-    d4[2] = -w;
-    d4[3] = q.ga * q.room;
-  } else {
-    const YPath q = y_path(a.z.y[idx], a.p.lc[idx], a.p.uc[idx], a.z.ax[idx]);
-    const double ay = fabs(q.y);
-    if (which == 1) {
-      *bp = ay / (om * fabs(q.k1));
-      const double w = om * q.k1 * q.k1;
-      d4[0] = -w;
-      d4[1] = q.y * q.y * (1.0 / om);
-      d4[2] = -w;
-      d4[3] = -q.k1 * q.y;
-    } else {
-      *bp = ay / (om * fabs(q.k2));
-      const double w = om * q.k2 * q.k2;
-      d4[0] = w;
-      d4[1] = -q.y * q.y * (1.0 / om);
-      d4[2] = w;
-      d4[3] = q.k2 * q.y;
-    }
-  }
+  if (which == 0)
+    x_cand(x_path(a.z.x[idx], a.p.c[idx], a.z.aty[idx], a.p.lv[idx], a.p.uv[idx]), om, bp, d4);
+  else
+    y_cand(y_path(a.z.y[idx], a.p.lc[idx], a.p.uc[idx], a.z.ax[idx]), which, om, bp, d4);
 }
 
 constexpr int kFinPer = kGapCandCap / kThreads;

@@ -1,12 +1,17 @@
-// Host-side decisions of the restart scheme (Sec. 3, "Adaptive restarts") and of the
-// primal weight update (Algorithm 3), in plain C++ (no CUDA) so that they compile and
-// can be tested without a GPU.  The solver calls these; the device computes the gap
-// values and distances they take.
+// Decisions of the restart scheme (Sec. 3, "Adaptive restarts") and of the primal
+// weight update (Algorithm 3), in plain C++ so that they compile and can be tested
+// without a GPU.  The single-LP solver calls these on the host; the persistent batch
+// kernel calls the same functions on the device (nvcc marks them __host__ __device__).
 #pragma once
 
-#include <cmath>
-#include <cstdint>
-#include <limits>
+#include <math.h>
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define PDLP_HD __host__ __device__
+#else
+#define PDLP_HD
+#endif
 
 namespace pdlp {
 
@@ -16,13 +21,13 @@ namespace pdlp {
 // exceeds 2^52 (no run gets that far; beyond it the doubles of the test below no
 // longer resolve single iterations).  The host synchronises with the device at that
 // iteration at the latest.
-inline int64_t steps_to_artificial(int64_t k, int64_t t, double beta_art) {
-  const int64_t never = std::numeric_limits<int64_t>::max() / 4;
+PDLP_HD inline int64_t steps_to_artificial(int64_t k, int64_t t, double beta_art) {
+  const int64_t never = INT64_MAX / 4;
   if (!(beta_art < 1.0)) return never;
   int64_t j = 1;
   const double need = (beta_art * (double)k - (double)t) / (1.0 - beta_art);
   if (!(need < 4503599627370496.0)) return never;  // 2^52, NaN included
-  if (need > 1.0) j = (int64_t)std::ceil(need);
+  if (need > 1.0) j = (int64_t)ceil(need);
   // the estimate may be off by rounding: settle on the first j that satisfies the test
   while (j > 1 && (double)(t + j - 1) >= beta_art * (double)(k + j - 1)) --j;
   while (!((double)(t + j) >= beta_art * (double)(k + j))) ++j;
@@ -34,7 +39,7 @@ inline int64_t steps_to_artificial(int64_t k, int64_t t, double beta_art) {
 // periodic checks and once mu(z^{n,0}, z^{n-1,0}) exists; (i) before (ii); (iii) only
 // when neither holds.  mu_c_prev is the candidate gap of the previous check in the same
 // outer loop (+inf if none).
-inline int restart_kind(bool is_check, bool is_art, bool have_mu_ref, double mu_c,
+PDLP_HD inline int restart_kind(bool is_check, bool is_art, bool have_mu_ref, double mu_c,
                         double mu_ref, double mu_c_prev, double beta_suff, double beta_nec) {
   int kind = 0;
   if (is_check && have_mu_ref) {
@@ -49,9 +54,9 @@ inline int restart_kind(bool is_check, bool is_art, bool have_mu_ref, double mu_
 
 // Algorithm 3: omega <- exp(theta log(dy / dx) + (1 - theta) log(omega)) when both
 // distances moved by the restart lie in (eps_zero, 1 / eps_zero); else omega unchanged.
-inline double primal_weight(double omega, double dx, double dy, double theta, double eps_zero) {
+PDLP_HD inline double primal_weight(double omega, double dx, double dy, double theta, double eps_zero) {
   if (eps_zero < dx && dx < 1.0 / eps_zero && eps_zero < dy && dy < 1.0 / eps_zero)
-    return std::exp(theta * std::log(dy / dx) + (1.0 - theta) * std::log(omega));
+    return exp(theta * log(dy / dx) + (1.0 - theta) * log(omega));
   return omega;
 }
 

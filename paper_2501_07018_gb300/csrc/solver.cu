@@ -8,6 +8,7 @@
 // counts where something else happens -- every check_period accepted iterations
 // (termination and restart evaluation), and whenever restart condition (iii) can fire
 // -- which it computes in advance from (k, t).
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cstdio>
@@ -22,6 +23,7 @@
 
 #include "../../include/pdlp.h"
 #include "adjoint.cuh"
+#include "batch.cuh"
 #include "gap.cuh"
 #include "graph.cuh"
 #include "host_logic.h"
@@ -1391,6 +1393,19 @@ struct StreamGuard {
   }
 };
 
+static void check_params(const pdlp_params& prm) {
+  if (prm.pc_alpha >= 2.0) throw PdlpError(-1, "pc_alpha must be < 2");
+  if (prm.max_iters < 1 || prm.check_period < 1 || prm.max_step_retries < 1)
+    throw PdlpError(-1, "max_iters, check_period and max_step_retries must be >= 1");
+  if (prm.termination_mode < 0 || prm.termination_mode > 2)
+    throw PdlpError(-1, "termination_mode must be 0, 1 or 2");
+  if (!(prm.beta_art >= 0.0) || std::isnan(prm.beta_suff) || std::isnan(prm.beta_nec))
+    throw PdlpError(-1, "beta_art must be >= 0 (>= 1: criterion (iii) off); beta_suff and beta_nec not NaN");
+  if (!(prm.fixed_step >= 0.0 && std::isfinite(prm.fixed_step)) ||
+      !(prm.fixed_omega >= 0.0 && std::isfinite(prm.fixed_omega)))
+    throw PdlpError(-1, "fixed_step and fixed_omega must be finite and >= 0");
+}
+
 static Inputs make_inputs(int64_t m, int64_t n, const pdlp_csr* A, const double* c,
                           const double* lc, const double* uc, const double* lv, const double* uv,
                           const pdlp_params* p) {
@@ -1472,6 +1487,358 @@ static int run_batch(const char* name, int64_t count, const pdlp_params& prm, in
 }
 }  // namespace pdlp
 
+
+// ---------------------------------------------------------------------------
+// persistent batch: every LP set up by the single-LP code (staging, validation,
+// preconditioning, SELL layouts) on worker streams, then one launch of k_batch
+// ---------------------------------------------------------------------------
+namespace pdlp {
+
+template <class T>
+struct BatchItem {
+  DeviceArena arena;
+  Problem<T> P;
+  BatchLP<T> d{};
+  double *dx = nullptr, *dy = nullptr;  // device outputs when the caller's are on the host
+  int code = 0;                         // negative: the LP failed before the launch
+  std::string err;
+  double setup_s = 0.0;
+  int64_t launches = 0;
+};
+
+__global__ void k_narrow_u16(const int32_t* in, uint16_t* out, int64_t len) {
+  for (int64_t i = sgi(); i < len; i += sgs()) out[i] = (uint16_t)in[i];
+}
+
+// 16-bit copy of a SELL layout's column indices (every index < cols <= 65536)
+template <class T>
+static const uint16_t* sell_col16(DeviceArena& a, const Mat<T>& M, cudaStream_t s) {
+  uint16_t* out = a.alloc<uint16_t>(M.sell_entries);
+  if (M.sell_entries) {
+    k_narrow_u16<<<vec_grid(M.sell_entries), kThreads, 0, s>>>(M.sell_col, out, M.sell_entries);
+    PDLP_LAUNCH_CHECK();
+  }
+  return out;
+}
+
+// LP i's problem, work buffers and descriptor, on stream s
+template <class T>
+static void batch_setup_one(BatchItem<T>& it, const pdlp_problem& pr, const pdlp_params& prm,
+                            cudaStream_t s) {
+  const auto t0 = Clock::now();
+  it.arena.set_stream(s);
+  const Inputs in = make_inputs(pr.m, pr.n, &pr.A, pr.c, pr.lc, pr.uc, pr.lv, pr.uv, &prm);
+  if (!pr.x_out || (pr.m > 0 && !pr.y_out)) throw PdlpError(-1, "null output array");
+  DeviceArena& a = it.arena;
+  DevInputs d = stage_inputs(a, in, s);
+  validate(a, in, d, s);
+  Problem<T>& P = it.P;
+  build_problem<T>(a, in, d, prm.ruiz_iters, prm.pc_alpha, P, s);
+  const int64_t m = P.m, n = P.n;
+  BatchLP<T>& L = it.d;
+  L.A = P.A;
+  L.AT = P.AT;
+  L.m = m;
+  L.n = n;
+  L.c = P.c;
+  L.lc = P.lc;
+  L.uc = P.uc;
+  L.lv = P.lv;
+  L.uv = P.uv;
+  L.o = OrigVecs{P.orig.c, P.orig.lc, P.orig.uc, P.orig.lv, P.orig.uv,
+                 P.d1,     P.d2,      P.inv_d1,  P.inv_d2};
+  L.perm_r = P.perm_r;
+  L.perm_c = P.perm_c;
+  L.c_norm = P.c_norm;
+  L.b_norm = P.b_norm;
+  L.eta0 = P.max_abs > 0.0 ? 1.0 / P.max_abs : 1.0;
+  L.omega0 = (P.c_norm_s > 0.0 && P.b_norm_s > 0.0) ? P.c_norm_s / P.b_norm_s : 1.0;
+  for (int q = 0; q < 2; ++q) {
+    L.X[q] = a.alloc<T>(n);
+    L.ATY[q] = a.alloc<T>(n);
+    L.Y[q] = a.alloc<T>(m);
+    L.AX[q] = a.alloc<T>(m);
+  }
+  using S = typename BatchSum<T>::type;
+  L.Sx = a.alloc<S>(n);
+  L.Sy = a.alloc<S>(m);
+  L.a_col16 = n <= 65536 ? sell_col16(a, P.A, s) : nullptr;
+  L.at_col16 = m <= 65536 ? sell_col16(a, P.AT, s) : nullptr;
+  L.gp_row = a.alloc<float4>(m);
+  L.gp_x = a.alloc<float>(3 * n);
+  L.X0 = a.alloc<T>(n);
+  L.Y0 = a.alloc<T>(m);
+  L.Xa = a.alloc<T>(n);
+  L.ATYa = a.alloc<T>(n);
+  L.Ya = a.alloc<T>(m);
+  L.AXa = a.alloc<T>(m);
+  if (prm.detect_infeasibility) {
+    L.yd = a.alloc<T>(m);
+    L.atyd = a.alloc<T>(n);
+    L.xb = a.alloc<T>(3 * n);
+    L.axb = a.alloc<T>(3 * m);
+  }
+  if (in.on_device) {
+    L.x_out = pr.x_out;
+    L.y_out = pr.y_out;
+  } else {
+    it.dx = a.alloc<double>(n);
+    it.dy = a.alloc<double>(m);
+    L.x_out = it.dx;
+    L.y_out = it.dy;
+  }
+  PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+  it.launches = P.launches;
+  it.setup_s = secs_since(t0);
+}
+
+// Work of one iteration of an LP (bytes of its two products and vectors, FP32 units),
+// the key of the largest-first order and of the autotuner's throughput.
+static double lp_work(int64_t m, int64_t n, int64_t nnz) {
+  return 2.0 * 8.0 * (double)nnz + 11.0 * 4.0 * (double)(m + n);
+}
+
+template <class T>
+static int batch_persistent(int64_t count, const pdlp_problem* problems, const pdlp_params& prm,
+                            int tune, int* status_out, pdlp_stats* stats_out, int* tune_out) {
+  const auto t_call = Clock::now();
+  int dev = 0;
+  PDLP_CUDA_CHECK(cudaGetDevice(&dev));
+  StreamGuard sg(prm.cuda_stream);
+  cudaStream_t s = sg.s;
+  // ---- setup of every LP on worker streams ----
+  std::vector<std::unique_ptr<BatchItem<T>>> items(count);
+  for (auto& p : items) p.reset(new BatchItem<T>());
+  {
+    const int64_t workers = std::max<int64_t>(1, std::min<int64_t>(16, count));
+    std::atomic<int64_t> next{0};
+    auto work = [&]() {
+      cudaStream_t ws = nullptr;
+      const bool ok = cudaSetDevice(dev) == cudaSuccess &&
+                      cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) == cudaSuccess;
+      for (;;) {
+        const int64_t i = next.fetch_add(1);
+        if (i >= count) break;
+        BatchItem<T>& it = *items[i];
+        if (!ok) {
+          it.code = PDLP_CUDA_ERROR;
+          it.err = "could not create a stream for a worker";
+          continue;
+        }
+        try {
+          batch_setup_one<T>(it, problems[i], prm, ws);
+        } catch (const PdlpError& e) {
+          it.code = e.code < 0 ? e.code : PDLP_CUDA_ERROR;
+          it.err = e.what();
+        } catch (const std::exception& e) {
+          it.code = PDLP_CUDA_ERROR;
+          it.err = e.what();
+        }
+        // the arena is released on the launch stream once the batch is done
+        if (ws) cudaStreamSynchronize(ws);
+        it.arena.set_stream(s);
+      }
+      if (ws) cudaStreamDestroy(ws);
+    };
+    std::vector<std::thread> pool;
+    for (int64_t w = 1; w < workers; ++w) pool.emplace_back(work);
+    work();
+    for (auto& t : pool) t.join();
+  }
+  std::vector<int32_t> order;
+  for (int64_t i = 0; i < count; ++i)
+    if (items[i]->code == 0) order.push_back((int32_t)i);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    const BatchLP<T>& x = items[a]->d;
+    const BatchLP<T>& y = items[b]->d;
+    return lp_work(x.m, x.n, x.A.nnz) > lp_work(y.m, y.n, y.A.nnz);
+  });
+  const int nv = (int)order.size();
+  double t_setup = secs_since(t_call);
+
+  DeviceArena arena;
+  arena.set_stream(s);
+  std::vector<BatchResult> hres(count);
+  int chosen = 1;
+  double tune_s = 0.0, launch_s = 0.0;
+  if (nv > 0) {
+    std::vector<BatchLP<T>> hd(count);
+    for (int64_t i = 0; i < count; ++i) hd[i] = items[i]->d;
+    BatchLP<T>* dl = arena.alloc<BatchLP<T>>(count);
+    int32_t* dord = arena.alloc<int32_t>(nv);
+    BatchResult* dres = arena.alloc<BatchResult>(count);
+    unsigned int* queue = arena.alloc<unsigned int>(1);
+    const int64_t tab_len = std::min<int64_t>(prm.max_iters + 1, (int64_t)1 << 16);
+    double* tab = arena.alloc<double>(2 * tab_len);
+    fill_step_table(tab, tab_len, s);
+    PDLP_CUDA_CHECK(cudaMemcpyAsync(dl, hd.data(), sizeof(BatchLP<T>) * count, cudaMemcpyHostToDevice, s));
+    PDLP_CUDA_CHECK(cudaMemcpyAsync(dord, order.data(), sizeof(int32_t) * nv, cudaMemcpyHostToDevice, s));
+    PDLP_CUDA_CHECK(cudaMemsetAsync(dres, 0, sizeof(BatchResult) * count, s));
+    BatchParams bp{};
+    bp.eps_rel_kkt = prm.eps_rel_kkt;
+    bp.eps_abs_feas = prm.eps_abs_feas;
+    bp.eps_rel_gap = prm.eps_rel_gap;
+    bp.termination_mode = prm.termination_mode;
+    bp.reduced_costs = prm.reduced_costs;
+    bp.check_period = prm.check_period;
+    bp.max_retries = prm.max_step_retries;
+    bp.detect_infeasibility = prm.detect_infeasibility;
+    bp.max_iters = prm.max_iters;
+    bp.time_limit_s = prm.time_limit_s;
+    bp.beta_suff = prm.beta_suff;
+    bp.beta_nec = prm.beta_nec;
+    bp.beta_art = prm.beta_art;
+    bp.theta = prm.theta;
+    bp.eps_zero = prm.eps_zero;
+    bp.fixed_step = prm.fixed_step;
+    bp.fixed_omega = prm.fixed_omega;
+    bp.eps_infeas = prm.eps_infeas;
+    bp.step_tab = tab;
+    bp.step_len = tab_len;
+
+    if (tune == 0) {
+      // Autotuner: time 128 iterations (checks included, termination off) of a sample
+      // of the batch spread over its size order under every launch configuration, and
+      // keep the one with the highest throughput (work of the iterations done divided
+      // by the time the LPs occupied their CTAs, per CTA slot of the device).
+      const auto t0 = Clock::now();
+      const int nconf = batch_config_count();
+      int ns = 1;
+      for (int c = 1; c <= nconf; ++c) ns = std::max(ns, batch_resident_ctas<T>(c));
+      ns = std::min(ns, nv);
+      std::vector<int32_t> samp(ns);
+      for (int q = 0; q < ns; ++q) samp[q] = order[(int64_t)q * nv / ns];
+      int32_t* dsamp = arena.alloc<int32_t>(ns);
+      BatchResult* pres = arena.alloc<BatchResult>(count);
+      PDLP_CUDA_CHECK(cudaMemcpyAsync(dsamp, samp.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, s));
+      BatchParams pp = bp;
+      pp.max_iters = 128;
+      pp.eps_rel_kkt = -1.0;
+      pp.termination_mode = 0;
+      pp.detect_infeasibility = 0;
+      pp.time_limit_s = INFINITY;
+      double best = -1.0;
+      std::vector<BatchResult> pr(count);
+      for (int c = 1; c <= nconf; ++c) {
+        PDLP_CUDA_CHECK(cudaMemsetAsync(queue, 0, sizeof(unsigned int), s));
+        const int slots = std::min(ns, batch_resident_ctas<T>(c));
+        launch_batch<T>(dl, dsamp, ns, pp, pres, queue, c, slots, s);
+        PDLP_CUDA_CHECK(cudaMemcpyAsync(pr.data(), pres, sizeof(BatchResult) * count, cudaMemcpyDeviceToHost, s));
+        PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+        double work = 0.0, secs = 0.0;
+        for (int q = 0; q < ns; ++q) {
+          const BatchLP<T>& L = hd[samp[q]];
+          work += lp_work(L.m, L.n, L.A.nnz) * (double)pr[samp[q]].k;
+          secs += pr[samp[q]].seconds;
+        }
+        // per CTA slot, times the LPs the real launch runs at once
+        const double rate =
+            secs > 0.0 ? work / secs * std::min(nv, batch_resident_ctas<T>(c)) : 0.0;
+        if (rate > best) {
+          best = rate;
+          chosen = c;
+        }
+      }
+      tune_s = secs_since(t0);
+    } else {
+      chosen = tune;
+    }
+    const int ctas = std::min(nv, batch_resident_ctas<T>(chosen));
+    PDLP_CUDA_CHECK(cudaMemsetAsync(queue, 0, sizeof(unsigned int), s));
+    cudaEvent_t ev[2];
+    PDLP_CUDA_CHECK(cudaEventCreate(&ev[0]));
+    PDLP_CUDA_CHECK(cudaEventCreate(&ev[1]));
+    PDLP_CUDA_CHECK(cudaEventRecord(ev[0], s));
+    launch_batch<T>(dl, dord, nv, bp, dres, queue, chosen, ctas, s);
+    PDLP_CUDA_CHECK(cudaEventRecord(ev[1], s));
+    PDLP_CUDA_CHECK(cudaMemcpyAsync(hres.data(), dres, sizeof(BatchResult) * count, cudaMemcpyDeviceToHost, s));
+    for (int q = 0; q < nv; ++q) {
+      const BatchItem<T>& it = *items[order[q]];
+      if (!it.dx) continue;
+      const pdlp_problem& pb = problems[order[q]];
+      PDLP_CUDA_CHECK(cudaMemcpyAsync(pb.x_out, it.dx, sizeof(double) * pb.n, cudaMemcpyDeviceToHost, s));
+      if (pb.m) PDLP_CUDA_CHECK(cudaMemcpyAsync(pb.y_out, it.dy, sizeof(double) * pb.m, cudaMemcpyDeviceToHost, s));
+    }
+    PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+    float ms = 0.0f;
+    PDLP_CUDA_CHECK(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+    launch_s = 1e-3 * ms;
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+  }
+  if (tune_out) *tune_out = chosen;
+  const double t_total = secs_since(t_call);
+  std::string first_error;
+  for (int64_t i = 0; i < count; ++i) {
+    const BatchItem<T>& it = *items[i];
+    if (it.code != 0) {
+      status_out[i] = it.code;
+      if (first_error.empty()) first_error = "problem " + std::to_string(i) + ": " + it.err;
+      if (stats_out) {
+        std::memset(&stats_out[i], 0, sizeof(pdlp_stats));
+        stats_out[i].status = it.code;
+      }
+      continue;
+    }
+    const BatchResult& r = hres[i];
+    status_out[i] = r.status;
+    if (!stats_out) continue;
+    pdlp_stats* st = &stats_out[i];
+    std::memset(st, 0, sizeof(*st));
+    st->status = r.status;
+    st->iterations = r.k;
+    st->attempts = r.attempts;
+    st->rejected_steps = r.rejected;
+    for (int q = 0; q < 3; ++q) st->restarts[q] = r.restarts[q];
+    st->kkt_passes = 0.5 * (double)(r.attempts + r.k);
+    st->rel_kkt = r.rel_kkt;
+    st->rel_primal = r.rel_primal;
+    st->rel_dual = r.rel_dual;
+    st->rel_gap = r.rel_gap;
+    st->primal_res_l2 = r.pres2;
+    st->dual_res_l2 = r.dres2;
+    st->primal_res_inf = r.pres_inf;
+    st->dual_res_inf = r.dres_inf;
+    st->pobj = r.pobj;
+    st->dobj = r.dobj;
+    st->paper_gap = r.paper_gap;
+    st->primal_res_rel_inf = r.pres_rel_inf;
+    st->dual_res_rel_inf = r.dres_rel_inf;
+    st->omega = r.omega;
+    st->eta_hat = r.eta_hat;
+    st->seconds_setup = it.setup_s;
+    st->seconds_solve = r.seconds;
+    st->seconds_total = t_total;
+    st->evaluations = r.evaluations;
+    st->gap_evals = r.gap_evals;
+    st->gap_fallbacks = r.gap_fallbacks;
+    st->gap_failures = r.gap_failures;
+    st->kernel_launches = it.launches + 1;
+    st->device_bytes = (int64_t)it.arena.total();
+    const double v = (double)sizeof(T);
+    const int64_t m = it.P.m, n = it.P.n, nnz = it.P.nnz;
+    st->bytes_spmv_a = (double)(m + 1) * 8 + (double)nnz * (4 + v) + (double)n * v + 6.0 * m * v;
+    st->bytes_spmv_at = (double)(n + 1) * 8 + (double)nnz * (4 + v) + (double)m * v +
+                        6.0 * (double)n * v + 6.0 * (double)m * v;
+    // device time by phase (the LP's time split by its SM cycles per phase)
+    double cyc = 0.0;
+    for (int q = 0; q < 5; ++q) cyc += (double)r.cycles[q];
+    const double per = cyc > 0.0 ? 1e3 * r.seconds / cyc : 0.0;
+    st->ms_primal = per * (double)r.cycles[0];
+    st->ms_spmv_a = per * (double)r.cycles[1];
+    st->ms_spmv_at = per * (double)r.cycles[2];
+    st->ms_checks = per * (double)(r.cycles[3] + r.cycles[4]);
+    st->batch_launch_s = launch_s;
+    st->batch_sm = r.sm;
+  }
+  (void)tune_s;
+  (void)t_setup;
+  if (!first_error.empty()) set_last_error(first_error);
+  return 0;
+}
+
+}  // namespace pdlp
+
 extern "C" {
 
 void pdlp_params_default(pdlp_params* p) {
@@ -1520,16 +1887,7 @@ int pdlp_solve(int64_t m, int64_t n, const pdlp_csr* A, const double* c, const d
     if (p) prm = *p;
     const Inputs in = make_inputs(m, n, A, c, lc, uc, lv, uv, &prm);
     if (!x_out || (m > 0 && !y_out)) throw PdlpError(-1, "null output array");
-    if (prm.pc_alpha >= 2.0) throw PdlpError(-1, "pc_alpha must be < 2");
-    if (prm.max_iters < 1 || prm.check_period < 1 || prm.max_step_retries < 1)
-      throw PdlpError(-1, "max_iters, check_period and max_step_retries must be >= 1");
-    if (prm.termination_mode < 0 || prm.termination_mode > 2)
-      throw PdlpError(-1, "termination_mode must be 0, 1 or 2");
-    if (!(prm.beta_art >= 0.0) || std::isnan(prm.beta_suff) || std::isnan(prm.beta_nec))
-      throw PdlpError(-1, "beta_art must be >= 0 (>= 1: criterion (iii) off); beta_suff and beta_nec not NaN");
-    if (!(prm.fixed_step >= 0.0 && std::isfinite(prm.fixed_step)) ||
-        !(prm.fixed_omega >= 0.0 && std::isfinite(prm.fixed_omega)))
-      throw PdlpError(-1, "fixed_step and fixed_omega must be finite and >= 0");
+    check_params(prm);
     StreamGuard sg(prm.cuda_stream);
     if (prm.precision == PDLP_FP32_BULK) {
       Solver<float> S(prm, sg.s);
@@ -1561,6 +1919,31 @@ int pdlp_solve_batch(int64_t count, const pdlp_problem* problems, const pdlp_par
                        return pdlp_solve(pb.m, pb.n, &pb.A, pb.c, pb.lc, pb.uc, pb.lv, pb.uv, &q,
                                          pb.x_out, pb.y_out, stats_out ? &stats_out[i] : nullptr);
                      });
+  } catch (...) {
+    return handle_exception();
+  }
+}
+
+int pdlp_solve_batch_persistent(int64_t count, const pdlp_problem* problems, const pdlp_params* p,
+                                int tune, int* status_out, pdlp_stats* stats_out, int* tune_out) {
+  try {
+    if (count < 0) throw PdlpError(-1, "pdlp_solve_batch_persistent: count < 0");
+    if (count > INT32_MAX) throw PdlpError(-1, "pdlp_solve_batch_persistent: count > 2^31-1");
+    if (count > 0 && (!problems || !status_out))
+      throw PdlpError(-1, "pdlp_solve_batch_persistent: null problems or status_out");
+    pdlp_params prm;
+    pdlp_params_default(&prm);
+    if (p) prm = *p;
+    check_params(prm);
+    if (prm.feasibility_polishing)
+      throw PdlpError(-1, "pdlp_solve_batch_persistent: feasibility polishing is not available "
+                          "in the persistent batch (use pdlp_solve_batch)");
+    if (tune < 0 || tune > batch_config_count())
+      throw PdlpError(-1, "tune must be 0 (autotune) or a configuration 1.." +
+                              std::to_string(batch_config_count()));
+    if (prm.precision == PDLP_FP32_BULK)
+      return batch_persistent<float>(count, problems, prm, tune, status_out, stats_out, tune_out);
+    return batch_persistent<double>(count, problems, prm, tune, status_out, stats_out, tune_out);
   } catch (...) {
     return handle_exception();
   }
