@@ -301,8 +301,9 @@ int pdlp_solve_batch(int64_t count, const pdlp_problem* problems, const pdlp_par
  * (preconditioning, layouts) runs per LP on 16 worker streams first.  The vectors the
  * two sparse products gather are held in shared memory when an LP's fit (x' and y',
  * else the one that fits, x' first).
- *   tune: 0 = autotune -- time 128 iterations of a sample of the batch (spread over
- *   its sizes) under every launch configuration and solve with the fastest; 1..6 = that
+ *   tune: 0 = autotune -- time three check periods of iterations of a sample of the
+ *   batch (spread over its sizes) under every launch configuration and solve with the
+ *   fastest; 1..6 = that
  *   configuration (threads per CTA / CTAs per SM / shared memory per CTA / staging):
  *   1 = 1024/1/200 KB/on, 2 = 1024/1/200 KB/off, 3 = 768/1/200 KB/on, 4 = 512/1/200 KB/on,
  *   5 = 512/2/100 KB/on, 6 = 512/2/100 KB/off.  tune_out (may be NULL) receives the

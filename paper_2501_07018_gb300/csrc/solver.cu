@@ -1697,10 +1697,14 @@ static int batch_persistent(int64_t count, const pdlp_problem* problems, const p
     bp.step_len = tab_len;
 
     if (tune == 0) {
-      // Autotuner: time 128 iterations (checks included, termination off) of a sample
-      // of the batch spread over its size order under every launch configuration, and
-      // keep the one with the highest throughput (work of the iterations done divided
-      // by the time the LPs occupied their CTAs, per CTA slot of the device).
+      // Autotuner: time 192 iterations (termination off) of a sample of the batch spread
+      // over its size order under every launch configuration, and keep the one with the
+      // highest throughput (work of the iterations done divided by the time the LPs
+      // occupied their CTAs, per CTA slot of the device).  Restart criterion (iii) is
+      // off in the probe, so it evaluates at the periodic checks only -- one evaluation
+      // per check_period iterations, the mix of a long solve (with (iii), the first 128
+      // iterations of an LP hold 8 evaluations, which ranked the configurations by
+      // their evaluation cost).
       const auto t0 = Clock::now();
       const int nconf = batch_config_count();
       int ns = 1;
@@ -1712,7 +1716,8 @@ static int batch_persistent(int64_t count, const pdlp_problem* problems, const p
       BatchResult* pres = arena.alloc<BatchResult>(count);
       PDLP_CUDA_CHECK(cudaMemcpyAsync(dsamp, samp.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, s));
       BatchParams pp = bp;
-      pp.max_iters = 128;
+      pp.max_iters = std::min<int64_t>(3 * (int64_t)std::max(1, prm.check_period), 512);
+      pp.beta_art = 1.0;
       pp.eps_rel_kkt = -1.0;
       pp.termination_mode = 0;
       pp.detect_infeasibility = 0;
