@@ -180,8 +180,10 @@ typedef struct {
   int64_t polish_pauses;   /* Algorithm 4: pauses of normal PDLP                     */
   int64_t polish_primal_iters, polish_dual_iters; /* iterations of all phases      */
   int64_t polish_accepted_k; /* k of the pause whose pair was returned, else 0     */
-  int64_t device_bytes;    /* device memory the call allocated (stream-ordered; all of
-                              it is held until the call returns, so this is its peak) */
+  int64_t device_bytes;    /* peak device memory the call held (stream-ordered
+                              allocations; setup temporaries -- the staged input, the
+                              transpose, the preconditioner's and renumbering scratch --
+                              are freed once the layouts exist) */
   /* wall-clock milliseconds of the periodic checks (device work and the host
      synchronisations they need): normalized duality gaps, KKT measures, infeasibility
      tests, and the number of evaluation points (checks, (iii) iterations, restarts) */

@@ -47,6 +47,12 @@ constexpr BatchConfig kConfigs[] = {
 };
 constexpr int kNumConfigs = (int)(sizeof(kConfigs) / sizeof(kConfigs[0]));
 
+// entries per lane in flight in the products: 8 with 128 registers per thread, fewer
+// where a thread has 64 or 80
+#ifndef PDLP_BATCH_B_SMALL_REGS
+#define PDLP_BATCH_B_SMALL_REGS 4
+#endif
+
 enum { kGActive = 0, kGDone = 1, kGFailed = 2, kGNeedMore = 3 };
 enum { kGeo = 0, kLin = 1 };
 enum { kEpPlain = 0, kEpDual = 1, kEpAvg = 2 };
@@ -1484,7 +1490,7 @@ __global__ void __launch_bounds__(NT, PER_SM)
       for (int w = threadIdx.x; w < words; w += NT) dstw[w] = srcw[w];
     }
     __syncthreads();
-    solve_lp<T, NT, (NT * PER_SM >= 768 ? 4 : 8)>(lp, prm, res + idx, sh, dsm, stage_bytes);
+    solve_lp<T, NT, (NT * PER_SM >= 768 ? PDLP_BATCH_B_SMALL_REGS : 8)>(lp, prm, res + idx, sh, dsm, stage_bytes);
   }
 }
 

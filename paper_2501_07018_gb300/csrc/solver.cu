@@ -303,10 +303,44 @@ static void norms2(Problem<T>& P, const V* c, const V* lc, const V* uc, double* 
   PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
 }
 
+// Keeps the CSR prefix of a renumbered matrix that the kernels still read after setup
+// (the long rows [0, R0), processed in chunks) in arrays of `arena`, so that the full
+// renumbered CSR can be freed with the other setup temporaries.
+template <class T>
+static void keep_long_prefix(DeviceArena& arena, Mat<T>& M, cudaStream_t s) {
+  const int64_t R0 = M.R0;
+  int64_t ne = 0;
+  if (R0) {
+    PDLP_CUDA_CHECK(cudaMemcpyAsync(&ne, M.row_ptr + R0, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+  }
+  int64_t* rp = arena.alloc<int64_t>(R0 + 1);
+  int32_t* col = arena.alloc<int32_t>(ne);
+  T* val = arena.alloc<T>(ne);
+  if (R0) {
+    PDLP_CUDA_CHECK(cudaMemcpyAsync(rp, M.row_ptr, sizeof(int64_t) * (R0 + 1), cudaMemcpyDeviceToDevice, s));
+  } else {
+    PDLP_CUDA_CHECK(cudaMemsetAsync(rp, 0, sizeof(int64_t), s));
+  }
+  if (ne) {
+    PDLP_CUDA_CHECK(cudaMemcpyAsync(col, M.col, sizeof(int32_t) * ne, cudaMemcpyDeviceToDevice, s));
+    PDLP_CUDA_CHECK(cudaMemcpyAsync(val, M.val, sizeof(T) * ne, cudaMemcpyDeviceToDevice, s));
+  }
+  M.row_ptr = rp;
+  M.col = col;
+  M.val = val;
+}
+
+// The preconditioned, renumbered problem of Sec. 3 with its SELL-32 / long-row layouts.
+// With `tmp`, every setup temporary (the transpose, the preconditioner's scratch, the
+// renumbered CSR copies, the scratch of sorts and scans) is allocated there and freed,
+// in stream order, before returning; the problem then holds the layouts, the long-row
+// prefixes, the permutations and the vectors only (P.val64 / P.valT64 are null).
 template <class T>
 static void build_problem(DeviceArena& arena, const Inputs& in, const DevInputs& d,
                           int ruiz_iters, double pc_alpha, Problem<T>& P, cudaStream_t s,
-                          bool renumber = true) {
+                          bool renumber = true, DeviceArena* tmp = nullptr) {
+  DeviceArena& ta = tmp ? *tmp : arena;
   P.m = in.m;
   P.n = in.n;
   P.nnz = in.nnz;
@@ -327,19 +361,19 @@ static void build_problem(DeviceArena& arena, const Inputs& in, const DevInputs&
   P.AT.rows = n;
   P.AT.cols = m;
   P.AT.nnz = nnz;
-  P.AT.row_ptr = arena.alloc<int64_t>(n + 1);
-  P.AT.col = arena.alloc<int32_t>(nnz);
-  P.valT64 = arena.alloc<double>(nnz);
-  transpose_csr(arena, d.row_ptr, d.col, d.val, m, n, nnz, P.AT.row_ptr, P.AT.col, P.valT64, s);
+  P.AT.row_ptr = ta.alloc<int64_t>(n + 1);
+  P.AT.col = ta.alloc<int32_t>(nnz);
+  P.valT64 = ta.alloc<double>(nnz);
+  transpose_csr(ta, d.row_ptr, d.col, d.val, m, n, nnz, P.AT.row_ptr, P.AT.col, P.valT64, s);
   P.launches += 10;
 
   // Sec. 3: Ruiz passes, then Pock-Chambolle
-  P.d1 = arena.alloc<double>(m);
-  P.d2 = arena.alloc<double>(n);
-  double* nr = arena.alloc<double>(m);
-  double* nc = arena.alloc<double>(n);
-  double* fr = arena.alloc<double>(m);
-  double* fs = arena.alloc<double>(n);
+  P.d1 = (renumber ? ta : arena).alloc<double>(m);  // renumbered copies are kept below
+  P.d2 = (renumber ? ta : arena).alloc<double>(n);
+  double* nr = ta.alloc<double>(m);
+  double* nc = ta.alloc<double>(n);
+  double* fr = ta.alloc<double>(m);
+  double* fs = ta.alloc<double>(n);
   k_fill<<<vec_grid(m), kThreads, 0, s>>>(P.d1, m, 1.0);
   k_fill<<<vec_grid(n), kThreads, 0, s>>>(P.d2, n, 1.0);
   PDLP_LAUNCH_CHECK();
@@ -357,17 +391,17 @@ static void build_problem(DeviceArena& arena, const Inputs& in, const DevInputs&
     const double pr = 2.0 - pc_alpha, pcl = pc_alpha;
     pass(pr == 1.0 ? 1 : 2, pr, pcl == 1.0 ? 1 : 2, pcl);
   }
-  P.max_abs = max_abs(arena, P.val64, nnz, s);
+  P.max_abs = max_abs(ta, P.val64, nnz, s);
 
   if (!renumber) return;  // the preconditioner alone (original numbering)
 
   // renumber rows and columns by decreasing length, then the SELL-32 / long-row layout
   P.perm_r = arena.alloc<int32_t>(m);
-  P.inv_r = arena.alloc<int32_t>(m);
+  P.inv_r = ta.alloc<int32_t>(m);
   P.perm_c = arena.alloc<int32_t>(n);
-  P.inv_c = arena.alloc<int32_t>(n);
-  sort_by_length_desc(arena, P.A.row_ptr, m, P.perm_r, P.inv_r, s);
-  sort_by_length_desc(arena, P.AT.row_ptr, n, P.perm_c, P.inv_c, s);
+  P.inv_c = ta.alloc<int32_t>(n);
+  sort_by_length_desc(ta, P.A.row_ptr, m, P.perm_r, P.inv_r, s);
+  sort_by_length_desc(ta, P.AT.row_ptr, n, P.perm_c, P.inv_c, s);
   Mat<T> A2, AT2;
   A2.rows = m;
   A2.cols = n;
@@ -375,27 +409,31 @@ static void build_problem(DeviceArena& arena, const Inputs& in, const DevInputs&
   AT2.rows = n;
   AT2.cols = m;
   AT2.nnz = nnz;
-  A2.row_ptr = arena.alloc<int64_t>(m + 1);
-  A2.col = arena.alloc<int32_t>(nnz);
-  double* aval = arena.alloc<double>(nnz);
-  AT2.row_ptr = arena.alloc<int64_t>(n + 1);
-  AT2.col = arena.alloc<int32_t>(nnz);
-  double* atval = arena.alloc<double>(nnz);
-  permute_csr(arena, P.A.row_ptr, P.A.col, P.val64, m, P.perm_r, P.inv_c, A2.row_ptr, A2.col,
+  A2.row_ptr = ta.alloc<int64_t>(m + 1);
+  A2.col = ta.alloc<int32_t>(nnz);
+  double* aval = ta.alloc<double>(nnz);
+  AT2.row_ptr = ta.alloc<int64_t>(n + 1);
+  AT2.col = ta.alloc<int32_t>(nnz);
+  double* atval = ta.alloc<double>(nnz);
+  permute_csr(ta, P.A.row_ptr, P.A.col, P.val64, m, P.perm_r, P.inv_c, A2.row_ptr, A2.col,
               aval, s);
-  permute_csr(arena, P.AT.row_ptr, P.AT.col, P.valT64, n, P.perm_c, P.inv_r, AT2.row_ptr,
+  permute_csr(ta, P.AT.row_ptr, P.AT.col, P.valT64, n, P.perm_c, P.inv_r, AT2.row_ptr,
               AT2.col, atval, s);
   if (sizeof(T) == sizeof(double)) {
     A2.val = reinterpret_cast<T*>(aval);
     AT2.val = reinterpret_cast<T*>(atval);
   } else {
-    A2.val = arena.alloc<T>(nnz);
-    AT2.val = arena.alloc<T>(nnz);
+    A2.val = ta.alloc<T>(nnz);
+    AT2.val = ta.alloc<T>(nnz);
     convert_values<T>(aval, A2.val, nnz, s);
     convert_values<T>(atval, AT2.val, nnz, s);
   }
   build_sell<T>(arena, A2, aval, s);
   build_sell<T>(arena, AT2, atval, s);
+  if (tmp) {
+    keep_long_prefix<T>(arena, A2, s);
+    keep_long_prefix<T>(arena, AT2, s);
+  }
   P.A = A2;
   P.AT = AT2;
 
@@ -428,6 +466,16 @@ static void build_problem(DeviceArena& arena, const Inputs& in, const DevInputs&
   norms2<T, T>(P, P.c, P.lc, P.uc, o2, s);
   P.c_norm_s = std::sqrt(o2[0]);
   P.b_norm_s = std::sqrt(o2[1]);
+  if (tmp) {
+    tmp->release();  // stream-ordered: after every launch above that reads them
+    P.val64 = nullptr;
+    P.valT64 = nullptr;
+    P.inv_r = nullptr;
+    P.inv_c = nullptr;
+    P.orig.row_ptr = nullptr;
+    P.orig.col = nullptr;
+    P.orig.val = nullptr;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -595,6 +643,7 @@ struct Solver {
   EventTimer timer;
   GapStats gap_stats;
   int64_t launches = 0;
+  size_t setup_peak = 0;  // device bytes held at the end of setup, its temporaries included
   double ms_checks = 0.0;
   double ms_gap = 0.0, ms_kkt = 0.0, ms_infeas = 0.0;
   int64_t evaluations = 0;
@@ -1151,7 +1200,10 @@ struct Solver {
   PointRef<double> aux_pt{};
 
   void prepare_phases(const Inputs& in, const DevInputs& d, Clock::time_point t0) {
-    build_problem<T>(arena, in, d, prm.ruiz_iters, prm.pc_alpha, P, s);
+    DeviceArena tmp;
+    tmp.set_stream(s);
+    build_problem<T>(arena, in, d, prm.ruiz_iters, prm.pc_alpha, P, s, true, &tmp);
+    setup_peak = arena.total() + tmp.total();
     launches += P.launches;
     alloc_shared();
     alloc_polishing();
@@ -1232,18 +1284,25 @@ struct Solver {
 
   int run(const Inputs& in, double* x_out, double* y_out, pdlp_stats* st) {
     const auto t_start = Clock::now();
-    DevInputs d = stage_inputs(arena, in, s);
-    validate(arena, in, d, s);
+    // setup temporaries (the staged input included, unless the FP64 phase problem of
+    // FP32-bulk polishing is built from it later) are freed once the layouts exist
+    const bool keep_staged = prm.feasibility_polishing && !std::is_same<T, double>::value;
+    DeviceArena tmp;
+    tmp.set_stream(s);
+    DeviceArena& stage_arena = keep_staged ? arena : tmp;
+    DevInputs d = stage_inputs(stage_arena, in, s);
+    validate(stage_arena, in, d, s);
     in_ = &in;
     din_ = d;
-    if (prm.feasibility_polishing && !std::is_same<T, double>::value && in.nnz) {
+    if (keep_staged && in.nnz) {
       // build_problem scales the staged values in place; the FP64 phase problem is
       // built later from an unscaled copy
       double* v = arena.alloc<double>(in.nnz);
       PDLP_CUDA_CHECK(cudaMemcpyAsync(v, d.val, sizeof(double) * in.nnz, cudaMemcpyDeviceToDevice, s));
       din_.val = v;
     }
-    build_problem<T>(arena, in, d, prm.ruiz_iters, prm.pc_alpha, P, s);
+    build_problem<T>(arena, in, d, prm.ruiz_iters, prm.pc_alpha, P, s, true, &tmp);
+    setup_peak = arena.total() + tmp.total();
     launches += P.launches;
     alloc_shared();
     alloc_run(main_run);
@@ -1350,7 +1409,8 @@ struct Solver {
       st->polish_primal_iters = pol.primal_iters + (aux64 ? aux64->pol.primal_iters : 0);
       st->polish_dual_iters = pol.dual_iters + (aux64 ? aux64->pol.dual_iters : 0);
       st->polish_accepted_k = pol.accepted_k;
-      st->device_bytes = (int64_t)(arena.total() + (aux64 ? aux64->arena.total() : 0));
+      st->device_bytes = (int64_t)(std::max(setup_peak, arena.total()) +
+                                   (aux64 ? std::max(aux64->setup_peak, aux64->arena.total()) : 0));
     }
     return status;
   }
@@ -1530,10 +1590,12 @@ static void batch_setup_one(BatchItem<T>& it, const pdlp_problem& pr, const pdlp
   const Inputs in = make_inputs(pr.m, pr.n, &pr.A, pr.c, pr.lc, pr.uc, pr.lv, pr.uv, &prm);
   if (!pr.x_out || (pr.m > 0 && !pr.y_out)) throw PdlpError(-1, "null output array");
   DeviceArena& a = it.arena;
-  DevInputs d = stage_inputs(a, in, s);
-  validate(a, in, d, s);
+  DeviceArena tmp;  // the staged input and the setup temporaries, freed after setup
+  tmp.set_stream(s);
+  DevInputs d = stage_inputs(tmp, in, s);
+  validate(tmp, in, d, s);
   Problem<T>& P = it.P;
-  build_problem<T>(a, in, d, prm.ruiz_iters, prm.pc_alpha, P, s);
+  build_problem<T>(a, in, d, prm.ruiz_iters, prm.pc_alpha, P, s, true, &tmp);
   const int64_t m = P.m, n = P.n;
   BatchLP<T>& L = it.d;
   L.A = P.A;
