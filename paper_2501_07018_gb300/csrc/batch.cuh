@@ -1,4 +1,5 @@
-// Launch interface of the persistent batch kernel (batch.cu): many LPs solved by one
+// Launch interface of the persistent batch kernel (batch_impl.cuh, instantiated by
+// batch_f32.cu and batch_f64.cu): many LPs solved by one
 // launch, one CTA per LP at a time.
 #pragma once
 
@@ -67,7 +68,7 @@ struct BatchResult {
 };
 
 // Launch configurations 1..batch_config_count() (threads per CTA, CTAs per SM, shared
-// memory, staging; the table is in batch.cu and in include/pdlp.h).
+// memory, staging; the table is in batch_impl.cuh and in include/pdlp.h).
 int batch_config_count();
 // CTAs of configuration `config` resident at once on this device.
 template <class T>

@@ -1,4 +1,5 @@
-// Persistent batched PDLP: one launch solves many LPs of uneven sizes.
+// Persistent batched PDLP (templates; batch_f32.cu and batch_f64.cu instantiate them):
+// one launch solves many LPs of uneven sizes.
 //
 // Every CTA takes LPs from a device queue (largest first) and runs the whole method on
 // its LP alone, separated into phases by CTA barriers:
@@ -21,6 +22,8 @@
 // clock per SM), so scalar FP64 logic runs on one thread and is broadcast through
 // shared memory, and FP32-bulk reductions shuffle in FP32 before one FP64 sum across
 // warps.  Scalars that every thread needs are computed once by thread 0.
+#pragma once
+
 #include <math.h>
 
 #include "../../include/pdlp.h"
@@ -1496,8 +1499,6 @@ __global__ void __launch_bounds__(NT, PER_SM)
 
 }  // namespace
 
-int batch_config_count() { return kNumConfigs; }
-
 template <class T, int NT, int PER_SM>
 static int resident_impl(size_t smem) {
   static size_t set = 0;  // largest dynamic shared memory enabled so far
@@ -1545,12 +1546,5 @@ void launch_batch(const BatchLP<T>* lps, const int32_t* order, int count, const 
     k_batch<T, 512, 1><<<ctas, 512, smem, s>>>(lps, order, count, prm, res, queue, stage);
   PDLP_LAUNCH_CHECK();
 }
-
-template int batch_resident_ctas<double>(int);
-template int batch_resident_ctas<float>(int);
-template void launch_batch<double>(const BatchLP<double>*, const int32_t*, int, const BatchParams&,
-                                   BatchResult*, unsigned int*, int, int, cudaStream_t);
-template void launch_batch<float>(const BatchLP<float>*, const int32_t*, int, const BatchParams&,
-                                  BatchResult*, unsigned int*, int, int, cudaStream_t);
 
 }  // namespace pdlp

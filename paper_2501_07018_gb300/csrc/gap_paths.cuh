@@ -1,6 +1,6 @@
 // Per-coordinate paths of the maximiser in the normalized duality gap (Sec. 3,
 // "Adaptive restarts"), shared by the grid-wide kernels of gap.cu and the per-LP
-// evaluation of the persistent batch kernel (batch.cu).
+// evaluation of the persistent batch kernel (batch_impl.cuh).
 //
 // For z = (x, y) and radius r,
 //   r * rho_r(z) = max { L(x,yh) - L(xh,y) : zh in X x Y, ||zh - z||_omega <= r }.
