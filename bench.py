@@ -682,23 +682,33 @@ def adjoint_unrolled(pkg, count=256, K=2000, every=50, concurrency=16):
         items.append(dict(lp=inst, K=K, eta=0.9 / np.sqrt(a1 * ai), omega=1.0,
                           checkpoint_every=every, target=rng.uniform(0.0, 10.0, inst.n)))
     out = {"workload": f"{count} LPs m=2000 n=5000 (8 entries per column), K={K} steps, "
-                       f"checkpoint every {every}, {concurrency} in flight, host arrays"}
+                       f"checkpoint every {every}, host arrays; one persistent launch "
+                       f"(pdlp_unrolled_pdhg_batch_persistent) and {concurrency} concurrent "
+                       f"streams of single calls (pdlp_unrolled_pdhg_batch)"}
     grads = {}
-    for name, prec in (("fp32_forward", binding.FP32_BULK), ("fp64", binding.FP64)):
+    for name, prec, persistent in (("persistent_fp32_forward", binding.FP32_BULK, True),
+                                   ("persistent_fp64", binding.FP64, True),
+                                   ("fp32_forward", binding.FP32_BULK, False),
+                                   ("fp64", binding.FP64, False)):
         fw = [dict(it) for it in items]
         t0 = time.perf_counter()
-        got = binding.unrolled_pdhg_batch(fw, concurrency=concurrency, precision=prec)
+        got = binding.unrolled_pdhg_batch(fw, concurrency=concurrency, precision=prec,
+                                          persistent=persistent)
         t_fw = time.perf_counter() - t0
         bw = []
         for it, (_, x, _, _) in zip(items, got):
             bw.append(dict(it, gx=2.0 * (x - it["target"]), gy=np.zeros(it["lp"].m)))
         t0 = time.perf_counter()
-        got = binding.unrolled_pdhg_batch(bw, concurrency=concurrency, precision=prec)
+        got = binding.unrolled_pdhg_batch(bw, concurrency=concurrency, precision=prec,
+                                          persistent=persistent)
         t_fb = time.perf_counter() - t0
         ok = sum(1 for g in got if g[0] == 0 and np.all(np.isfinite(g[3]["c"])))
         grads[name] = [g[3]["c"] for g in got[:4]]
         out[name] = {"forward_s": t_fw, "forward_backward_s": t_fb,
                      "lps_per_s_forward_backward": count / t_fb, "ok": ok}
+    out["grad_c_rel_linf_persistent_vs_streams_fp64_first4"] = [
+        float(np.max(np.abs(a - b)) / max(1.0, float(np.max(np.abs(b)))))
+        for a, b in zip(grads["persistent_fp64"], grads["fp64"])]
     out["grad_c_rel_l2_fp32_vs_fp64_first4"] = [
         float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(grads["fp32_forward"], grads["fp64"])]
     return out

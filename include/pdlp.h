@@ -370,6 +370,21 @@ typedef struct {
 int pdlp_unrolled_pdhg_batch(int64_t count, const pdlp_unrolled_problem* problems,
                              const pdlp_params* p, int concurrency, int* status_out);
 
+/* The batch of pdlp_unrolled_pdhg_batch run by ONE persistent kernel launch: each CTA
+ * takes an LP from a device queue (the longest first) and runs its K steps of Eq. (3),
+ * the checkpoints and, with an upstream gradient, the reverse pass, on its own -- the
+ * computation of pdlp_unrolled_pdhg for that LP (each row's sum in the same entry order;
+ * rows longer than 4096 entries are summed in another order).  An LP's forward state and
+ * its two gathered FP64 adjoints live in the CTA's shared memory, so each LP must have
+ * 2 (m + n) forward values (FP64, or FP32 for PDLP_FP32_BULK) plus 8 (m + n) bytes within
+ * 200 KB (about m + n <= 8500 in FP64, 12800 with an FP32 forward); a larger LP fails
+ * alone with PDLP_INVALID_ARGUMENT.  params: precision, inputs_on_device and
+ * cuda_stream as pdlp_unrolled_pdhg; the rest is ignored.  status_out[count] receives
+ * each LP's return value.  Returns 0 when every LP was attempted (pdlp_last_error()
+ * then describes the first failed one), or PDLP_INVALID_ARGUMENT. */
+int pdlp_unrolled_pdhg_batch_persistent(int64_t count, const pdlp_unrolled_problem* problems,
+                                        const pdlp_params* p, int* status_out);
+
 /* Message for the last nonzero return of a call made by this thread. */
 const char* pdlp_last_error(void);
 

@@ -152,6 +152,8 @@ def load_library(path: str | None = None):
                                        ctypes.POINTER(Params), P, P, P, P, P, P, P]
     lib.pdlp_unrolled_pdhg.restype = ctypes.c_int
     lib.pdlp_unrolled_pdhg_batch.argtypes = [i64, P, ctypes.POINTER(Params), ctypes.c_int, P]
+    lib.pdlp_unrolled_pdhg_batch_persistent.argtypes = [i64, P, ctypes.POINTER(Params), P]
+    lib.pdlp_unrolled_pdhg_batch_persistent.restype = ctypes.c_int
     lib.pdlp_gather_bench.argtypes = [ctypes.c_int, ctypes.c_int, i64, ctypes.c_int, i64,
                                       ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_int, P]
@@ -403,9 +405,11 @@ def unrolled_pdhg(m, n, row_ptr, col_idx, val, c, lc, uc, lv, uv, K, eta, omega,
     return x, y, (grads if want else None)
 
 
-def unrolled_pdhg_batch(items, device: bool = False, concurrency: int = 16, **params) -> list:
-    """pdlp_unrolled_pdhg_batch.  ``items``: dicts with ``lp`` (an object with m, n and
-    the CSR/vector arrays), ``K``, ``eta``, ``omega`` and optionally ``gx``, ``gy``,
+def unrolled_pdhg_batch(items, device: bool = False, concurrency: int = 16,
+                        persistent: bool = False, **params) -> list:
+    """pdlp_unrolled_pdhg_batch (``persistent=True``: pdlp_unrolled_pdhg_batch_persistent,
+    one launch for the whole batch).  ``items``: dicts with ``lp`` (an object with m, n
+    and the CSR/vector arrays), ``K``, ``eta``, ``omega`` and optionally ``gx``, ``gy``,
     ``checkpoint_every``.  Returns, per item, (status, x, y, grads or None)."""
     lib = load_library()
     mh = _Marshal(device)
@@ -437,8 +441,12 @@ def unrolled_pdhg_batch(items, device: bool = False, concurrency: int = 16, **pa
         outs.append((x, y, grads))
     prm = _params_for(device, params)
     status = (ctypes.c_int * max(1, len(items)))()
-    _check(lib.pdlp_unrolled_pdhg_batch(len(items), ctypes.addressof(probs), ctypes.byref(prm),
-                                        int(concurrency), ctypes.addressof(status)))
+    if persistent:
+        _check(lib.pdlp_unrolled_pdhg_batch_persistent(len(items), ctypes.addressof(probs),
+                                                       ctypes.byref(prm), ctypes.addressof(status)))
+    else:
+        _check(lib.pdlp_unrolled_pdhg_batch(len(items), ctypes.addressof(probs), ctypes.byref(prm),
+                                            int(concurrency), ctypes.addressof(status)))
     return [(status[k], *outs[k]) for k in range(len(items))]
 
 

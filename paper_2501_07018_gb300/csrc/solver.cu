@@ -24,6 +24,7 @@
 #include "../../include/pdlp.h"
 #include "adjoint.cuh"
 #include "batch.cuh"
+#include "unroll_batch.cuh"
 #include "gap.cuh"
 #include "graph.cuh"
 #include "host_logic.h"
@@ -1906,6 +1907,209 @@ static int batch_persistent(int64_t count, const pdlp_problem* problems, const p
 
 }  // namespace pdlp
 
+
+// ---------------------------------------------------------------------------
+// persistent unrolled-PDHG batch: every LP set up as pdlp_unrolled_pdhg sets it up
+// (identity scaling, renumbered SELL layouts, FP32 copies for an FP32 forward) on worker
+// streams, then one launch of k_unroll_batch
+// ---------------------------------------------------------------------------
+namespace pdlp {
+
+template <class T>
+struct UnrollItem {
+  DeviceArena arena;
+  Problem<double> P;
+  Problem<float> P32;
+  UnrollLP<T> d{};
+  bool on_device = false;
+  double* host_out[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* dev_out[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int64_t out_len[7] = {0, 0, 0, 0, 0, 0, 0};
+  int code = 0;
+  std::string err;
+};
+
+template <class T>
+static void unroll_setup_one(UnrollItem<T>& it, const pdlp_unrolled_problem& u,
+                             const pdlp_params& prm, cudaStream_t s) {
+  it.arena.set_stream(s);
+  const Inputs in = make_inputs(u.m, u.n, &u.A, u.c, u.lc, u.uc, u.lv, u.uv, &prm);
+  if (u.K < 0) throw PdlpError(-1, "K < 0");
+  if (!(u.eta > 0.0) || !std::isfinite(u.eta) || !(u.omega > 0.0) || !std::isfinite(u.omega))
+    throw PdlpError(-1, "eta and omega must be positive and finite");
+  if (!u.x_out || (u.m > 0 && !u.y_out)) throw PdlpError(-1, "null output");
+  if (u.gx && u.m > 0 && !u.gy) throw PdlpError(-1, "gx without gy");
+  if (unroll_smem_need(u.m, u.n, sizeof(T)) > unroll_smem_max())
+    throw PdlpError(-1, "LP too large for the persistent unrolled batch (its state must fit "
+                        "one CTA's shared memory: 2 (m + n) forward values and m + n FP64 "
+                        "adjoints in " + std::to_string(unroll_smem_max()) +
+                        " bytes); use pdlp_unrolled_pdhg_batch");
+  DeviceArena& a = it.arena;
+  const int64_t m = u.m, n = u.n;
+  DevInputs d = stage_inputs(a, in, s);
+  validate(a, in, d, s);
+  build_problem<double>(a, in, d, 0, 0.0, it.P, s);  // identity scaling, renumbered
+  UnrollLP<T>& L = it.d;
+  L.m = m;
+  L.n = n;
+  L.K = u.K;
+  L.C = u.checkpoint_every > 0 ? u.checkpoint_every : 50;
+  L.tau = u.eta / u.omega;
+  L.sigma = u.eta * u.omega;
+  L.tau_t = (T)L.tau;
+  L.sigma_t = (T)L.sigma;
+  L.A64 = it.P.A;
+  L.AT64 = it.P.AT;
+  L.perm_r = it.P.perm_r;
+  L.perm_c = it.P.perm_c;
+  if constexpr (std::is_same<T, double>::value) {
+    L.A = it.P.A;
+    L.AT = it.P.AT;
+    L.c = it.P.c;
+    L.lc = it.P.lc;
+    L.uc = it.P.uc;
+    L.lv = it.P.lv;
+    L.uv = it.P.uv;
+  } else {
+    // FP32 forward: the same renumbered LP with FP32 values and vectors
+    build_problem<float>(a, in, d, 0, 0.0, it.P32, s);
+    L.A = it.P32.A;
+    L.AT = it.P32.AT;
+    L.c = it.P32.c;
+    L.lc = it.P32.lc;
+    L.uc = it.P32.uc;
+    L.lv = it.P32.lv;
+    L.uv = it.P32.uv;
+  }
+  const int64_t state = 2 * (m + n);
+  L.cp = a.alloc<T>((L.K / L.C + 1) * state);
+  L.seg = a.alloc<T>((L.C + 1) * state);
+  it.on_device = in.on_device;
+  // outputs: the caller's device arrays, or device arrays copied back after the launch
+  double* outs[7] = {u.x_out, u.y_out, u.grad_c, u.grad_lc, u.grad_uc, u.grad_lv, u.grad_uv};
+  const int64_t lens[7] = {n, m, n, m, m, n, n};
+  for (int q = 0; q < 7; ++q) {
+    it.out_len[q] = lens[q];
+    if (!outs[q] || (q >= 2 && !u.gx)) continue;
+    it.host_out[q] = outs[q];
+    it.dev_out[q] = in.on_device ? outs[q] : a.alloc<double>(lens[q]);
+  }
+  L.x_out = it.dev_out[0];
+  L.y_out = it.dev_out[1];
+  for (int q = 0; q < 5; ++q) L.gout[q] = it.dev_out[2 + q];
+  if (u.gx) {
+    // upstream gradient into the renumbered order
+    auto renumbered = [&](const double* src, int64_t len, const int32_t* perm) -> const double* {
+      if (!src || len == 0) return nullptr;
+      const double* dsrc = src;
+      if (!in.on_device) {
+        double* t = a.alloc<double>(len);
+        copy_in(t, src, sizeof(double) * len, false, s);
+        dsrc = t;
+      }
+      double* out = a.alloc<double>(len);
+      gather_f64(dsrc, perm, out, len, s);
+      return out;
+    };
+    L.gx = renumbered(u.gx, n, it.P.perm_c);
+    L.gy = renumbered(u.gy, m, it.P.perm_r);
+    L.bx = a.alloc<double>(n);
+    L.by = a.alloc<double>(m);
+    const int64_t glen[5] = {n, m, m, n, n};
+    for (int q = 0; q < 5; ++q) L.g[q] = a.alloc<double>(glen[q]);
+  }
+  PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+}
+
+template <class T>
+static int unroll_batch_persistent(int64_t count, const pdlp_unrolled_problem* problems,
+                                   const pdlp_params& prm, int* status_out) {
+  int dev = 0;
+  PDLP_CUDA_CHECK(cudaGetDevice(&dev));
+  StreamGuard sg(prm.cuda_stream);
+  cudaStream_t s = sg.s;
+  std::vector<std::unique_ptr<UnrollItem<T>>> items(count);
+  for (auto& p : items) p.reset(new UnrollItem<T>());
+  {
+    const int64_t workers = std::max<int64_t>(1, std::min<int64_t>(16, count));
+    std::atomic<int64_t> next{0};
+    auto work = [&]() {
+      cudaStream_t ws = nullptr;
+      const bool ok = cudaSetDevice(dev) == cudaSuccess &&
+                      cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) == cudaSuccess;
+      for (;;) {
+        const int64_t i = next.fetch_add(1);
+        if (i >= count) break;
+        UnrollItem<T>& it = *items[i];
+        if (!ok) {
+          it.code = PDLP_CUDA_ERROR;
+          it.err = "could not create a stream for a worker";
+          continue;
+        }
+        try {
+          unroll_setup_one<T>(it, problems[i], prm, ws);
+        } catch (const PdlpError& e) {
+          it.code = e.code < 0 ? e.code : PDLP_CUDA_ERROR;
+          it.err = e.what();
+        } catch (const std::exception& e) {
+          it.code = PDLP_CUDA_ERROR;
+          it.err = e.what();
+        }
+        if (ws) cudaStreamSynchronize(ws);
+        it.arena.set_stream(s);
+      }
+      if (ws) cudaStreamDestroy(ws);
+    };
+    std::vector<std::thread> pool;
+    for (int64_t w = 1; w < workers; ++w) pool.emplace_back(work);
+    work();
+    for (auto& t : pool) t.join();
+  }
+  std::vector<int32_t> order;
+  for (int64_t i = 0; i < count; ++i)
+    if (items[i]->code == 0) order.push_back((int32_t)i);
+  // the longest runs first: steps times the work of one step
+  auto work_of = [&](int32_t i) {
+    const UnrollLP<T>& L = items[i]->d;
+    return (double)(L.K + 1) * (double)(L.A.nnz + L.m + L.n) * (L.gx ? 4.0 : 1.0);
+  };
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int32_t a, int32_t b) { return work_of(a) > work_of(b); });
+  const int nv = (int)order.size();
+  DeviceArena arena;
+  arena.set_stream(s);
+  if (nv > 0) {
+    std::vector<UnrollLP<T>> hd(count);
+    for (int64_t i = 0; i < count; ++i) hd[i] = items[i]->d;
+    UnrollLP<T>* dl = arena.alloc<UnrollLP<T>>(count);
+    int32_t* dord = arena.alloc<int32_t>(nv);
+    unsigned int* queue = arena.alloc<unsigned int>(1);
+    PDLP_CUDA_CHECK(cudaMemcpyAsync(dl, hd.data(), sizeof(UnrollLP<T>) * count, cudaMemcpyHostToDevice, s));
+    PDLP_CUDA_CHECK(cudaMemcpyAsync(dord, order.data(), sizeof(int32_t) * nv, cudaMemcpyHostToDevice, s));
+    PDLP_CUDA_CHECK(cudaMemsetAsync(queue, 0, sizeof(unsigned int), s));
+    launch_unroll_batch<T>(dl, dord, nv, queue, std::min(nv, unroll_resident_ctas<T>()), s);
+    for (int q = 0; q < nv; ++q) {
+      const UnrollItem<T>& it = *items[order[q]];
+      if (it.on_device) continue;
+      for (int k = 0; k < 7; ++k)
+        if (it.host_out[k] && it.out_len[k] > 0)
+          PDLP_CUDA_CHECK(cudaMemcpyAsync(it.host_out[k], it.dev_out[k], sizeof(double) * it.out_len[k],
+                                          cudaMemcpyDeviceToHost, s));
+    }
+    PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+  }
+  std::string first_error;
+  for (int64_t i = 0; i < count; ++i) {
+    status_out[i] = items[i]->code;
+    if (items[i]->code != 0 && first_error.empty())
+      first_error = "problem " + std::to_string(i) + ": " + items[i]->err;
+  }
+  if (!first_error.empty()) set_last_error(first_error);
+  return 0;
+}
+
+}  // namespace pdlp
+
 extern "C" {
 
 void pdlp_params_default(pdlp_params* p) {
@@ -1944,6 +2148,26 @@ void pdlp_params_default(pdlp_params* p) {
 }
 
 const char* pdlp_last_error(void) { return g_last_error; }
+
+int pdlp_unrolled_pdhg_batch_persistent(int64_t count, const pdlp_unrolled_problem* problems,
+                                        const pdlp_params* p, int* status_out) {
+  try {
+    if (count < 0) throw PdlpError(-1, "pdlp_unrolled_pdhg_batch_persistent: count < 0");
+    if (count > INT32_MAX)
+      throw PdlpError(-1, "pdlp_unrolled_pdhg_batch_persistent: count > 2^31-1");
+    if (count > 0 && (!problems || !status_out))
+      throw PdlpError(-1, "pdlp_unrolled_pdhg_batch_persistent: null problems or status_out");
+    pdlp_params prm;
+    pdlp_params_default(&prm);
+    if (p) prm = *p;
+    if (prm.precision == PDLP_FP32_BULK)
+      return unroll_batch_persistent<float>(count, problems, prm, status_out);
+    return unroll_batch_persistent<double>(count, problems, prm, status_out);
+  } catch (...) {
+    return handle_exception();
+  }
+}
+
 
 int pdlp_solve(int64_t m, int64_t n, const pdlp_csr* A, const double* c, const double* lc,
                const double* uc, const double* lv, const double* uv, const pdlp_params* p,

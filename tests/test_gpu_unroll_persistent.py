@@ -1,0 +1,150 @@
+"""The persistent unrolled-PDHG batch (pdlp_unrolled_pdhg_batch_persistent): one launch,
+one CTA per LP, each LP's K fixed steps of Eq. (3), checkpoints and reverse pass -- held
+to the oracle's reverse-mode derivative at the tolerance of the single-call tests
+(1e-9 relative to the largest entry), to the single calls themselves (the same per-row
+summation order: 1e-12), and to its own recomputation from checkpoints (bit for bit
+across checkpoint spacings)."""
+import numpy as np
+import pytest
+
+import lpgen
+from oracle import pdlp_oracle as O
+from tests import test_oracle_adjoint as PA
+
+pytestmark = pytest.mark.gpu
+KEYS = ("c", "lc", "uc", "lv", "uv")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2501_07018_gb300 as p
+
+    return p
+
+
+def _close(a, b, rel):
+    scale = max(1.0, float(np.max(np.abs(b)))) if b.size else 1.0
+    return float(np.max(np.abs(a - b))) <= rel * scale if b.size else True
+
+
+def _single(pkg, it, **prm):
+    inst = it["lp"]
+    return pkg.binding.unrolled_pdhg(inst.m, inst.n, inst.row_ptr, inst.col_idx, inst.val,
+                                     inst.c, inst.lc, inst.uc, inst.lv, inst.uv, it["K"],
+                                     it["eta"], it.get("omega", 1.0), gx=it.get("gx"),
+                                     gy=it.get("gy"), checkpoint_every=it.get("checkpoint_every", 50),
+                                     **prm)
+
+
+def _items(seeds=(5, 6, 7), K=150, every=9):
+    items = []
+    for seed in seeds:
+        for inst in PA._fd_cases(seed):
+            rng = np.random.default_rng(seed)
+            eta = 0.9 / np.linalg.norm(inst.scipy_csr().toarray(), 2)
+            items.append(dict(lp=inst, K=K, eta=eta, omega=0.8, gx=rng.standard_normal(inst.n),
+                              gy=rng.standard_normal(inst.m), checkpoint_every=every))
+    return items
+
+
+def test_matches_oracle_and_single_calls(pkg):
+    items = _items()
+    items.append(dict(lp=items[0]["lp"], K=150, eta=items[0]["eta"], omega=0.8))  # forward only
+    got = pkg.binding.unrolled_pdhg_batch(items, persistent=True)
+    for it, (st, x, y, g) in zip(items, got):
+        assert st == 0
+        inst = it["lp"]
+        one = _single(pkg, it)
+        assert _close(x, one[0], 1e-12) and _close(y, one[1], 1e-12), inst.name
+        if it.get("gx") is None:
+            assert g is None
+            continue
+        xo, yo, go = O.unrolled_pdhg_vjp(inst, it["K"], it["eta"], it["omega"], it["gx"], it["gy"])
+        assert _close(x, xo, 1e-9) and _close(y, yo, 1e-9), inst.name
+        for k in KEYS:
+            assert _close(g[k], go[k], 1e-9), (inst.name, k)
+            assert _close(g[k], one[2][k], 1e-12), (inst.name, k)
+
+
+def test_checkpoint_spacings_recompute_bit_for_bit(pkg):
+    base = _items(seeds=(8,), K=100)
+    ref = None
+    for every in (1, 7, 50, 1000):
+        items = [dict(it, checkpoint_every=every) for it in base]
+        got = pkg.binding.unrolled_pdhg_batch(items, persistent=True)
+        if ref is None:
+            ref = got
+            continue
+        for (st, x, y, g), (_, xr, yr, gr) in zip(got, ref):
+            assert st == 0 and np.array_equal(x, xr) and np.array_equal(y, yr)
+            for k in KEYS:
+                assert np.array_equal(g[k], gr[k]), (every, k)
+
+
+def _config3_item(k):
+    rng = np.random.default_rng(lpgen.config_seed(3) + k)
+    inst = lpgen.random_lp(2000, 5000, 8, seed=lpgen.config_seed(3, k))
+    A = inst.scipy_csr()
+    eta = 0.9 / np.sqrt(float(abs(A).sum(axis=0).max()) * float(abs(A).sum(axis=1).max()))
+    K = 2000
+    target = rng.uniform(0.0, 10.0, inst.n)
+    xK = O.unrolled_pdhg(inst, K, eta, 1.0)[K][0]
+    return dict(lp=inst, K=K, eta=eta, omega=1.0, gx=2.0 * (xK - target), gy=np.zeros(inst.m),
+                checkpoint_every=50)
+
+
+def test_differentiable_batch_shape_matches_oracle(pkg):
+    """Two LPs of the differentiable-batch shape (2000 x 5000, 8 entries per column,
+    K = 2000, checkpoints every 50, loss ||x_K - x_target||^2) in one launch, against
+    the oracle's reverse-mode derivative element by element; device arrays."""
+    import torch
+
+    items = [_config3_item(k) for k in (0, 1)]
+    dev = [dict(it, gx=torch.as_tensor(it["gx"]).cuda(), gy=torch.as_tensor(it["gy"]).cuda())
+           for it in items]
+    got = pkg.binding.unrolled_pdhg_batch(dev, device=True, persistent=True)
+    for it, (st, x, y, g) in zip(items, got):
+        assert st == 0
+        inst = it["lp"]
+        xo, yo, go = O.unrolled_pdhg_vjp(inst, it["K"], it["eta"], 1.0, it["gx"], it["gy"])
+        assert _close(x.cpu().numpy(), xo, 1e-9) and _close(y.cpu().numpy(), yo, 1e-9)
+        for k in KEYS:
+            assert _close(g[k].cpu().numpy(), go[k], 1e-9), k
+
+
+def test_fp32_forward_matches_single_call(pkg):
+    """FP32 forward with the FP64 reverse pass: the same arithmetic as the single call
+    (x_K within 1e-6, gradients within 1e-6 relative l2), and the FP64 oracle's
+    derivative in direction and size."""
+    it = _config3_item(0)
+    (st, x, y, g), = pkg.binding.unrolled_pdhg_batch([it], persistent=True, precision=pkg.FP32_BULK)
+    assert st == 0
+    xs, ys, gs = _single(pkg, it, precision=pkg.FP32_BULK)
+    assert _close(x, xs, 1e-6) and _close(y, ys, 1e-6)
+    _, _, go = O.unrolled_pdhg_vjp(it["lp"], it["K"], it["eta"], 1.0, it["gx"], it["gy"])
+    for k in KEYS:
+        a, b = g[k], go[k]
+        nb = float(np.linalg.norm(b))
+        if nb == 0.0:
+            assert float(np.linalg.norm(a)) == 0.0
+            continue
+        assert float(np.linalg.norm(a - gs[k])) <= 1e-6 * max(nb, 1e-300), k
+        assert float(np.linalg.norm(a - b)) / nb <= 1e-2, k
+        assert float(a @ b) / (float(np.linalg.norm(a)) * nb) >= 0.9999, k
+
+
+def test_an_lp_too_large_fails_alone(pkg):
+    small = _items(seeds=(5,), K=20)[0]
+    big = lpgen.random_lp(4000, 9000, 4, seed=17)  # 2 (m + n) FP64 values + adjoints > 200 KB
+    items = [small, dict(lp=big, K=5, eta=0.1, omega=1.0)]
+    got = pkg.binding.unrolled_pdhg_batch(items, persistent=True)
+    assert got[0][0] == 0
+    assert got[1][0] == -1
+    assert "too large" in pkg.binding.load_library().pdlp_last_error().decode()
