@@ -317,8 +317,9 @@ int pdlp_solve_batch(int64_t count, const pdlp_problem* problems, const pdlp_par
  *   seconds_solve is the LP's device time inside the launch, seconds_setup its setup,
  *   seconds_total the whole call; ms_primal, ms_spmv_a, ms_spmv_at and ms_checks split
  *   seconds_solve by phase (the primal step; A x' with the dual step and Algorithm 2;
- *   A'y' with the running sums; evaluation points, start and output), in proportion
- *   to the SM clock cycles the CTA spent in each.
+ *   A'y' with the running sums; evaluation points, start and output), and ms_gap,
+ *   ms_kkt, ms_infeas the evaluation points' normalized gaps, KKT measures and
+ *   infeasibility tests, in proportion to the SM clock cycles the CTA spent in each.
  * Returns 0 when every LP was attempted (see status_out), or a negative code for bad
  * arguments of the call itself. */
 int pdlp_solve_batch_persistent(int64_t count, const pdlp_problem* problems, const pdlp_params* p,

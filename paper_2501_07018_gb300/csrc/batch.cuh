@@ -63,8 +63,9 @@ struct BatchResult {
   double omega, eta_hat;
   double seconds;  // device time of the LP's solve (global timer)
   int64_t sm;      // SM that solved it
-  int64_t cycles[5];  // SM clock cycles by phase: primal step, A x' with the dual step and
-                      // Algorithm 2, A'y' with the sums, evaluation points, rest
+  int64_t cycles[8];  // SM clock cycles by phase: primal step, A x' with the dual step and
+                      // Algorithm 2, A'y' with the sums, evaluation points (other work),
+                      // start and output, normalized gaps, KKT measures, infeasibility tests
 };
 
 // Launch configurations 1..batch_config_count() (threads per CTA, CTAs per SM, shared

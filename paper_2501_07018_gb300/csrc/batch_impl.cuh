@@ -55,6 +55,9 @@ constexpr int kNumConfigs = (int)(sizeof(kConfigs) / sizeof(kConfigs[0]));
 #ifndef PDLP_BATCH_B_SMALL_REGS
 #define PDLP_BATCH_B_SMALL_REGS 4
 #endif
+#ifndef PDLP_BATCH_B_THRESHOLD
+#define PDLP_BATCH_B_THRESHOLD 768
+#endif
 
 enum { kGActive = 0, kGDone = 1, kGFailed = 2, kGNeedMore = 3 };
 enum { kGeo = 0, kLin = 1 };
@@ -123,7 +126,7 @@ struct Sh {
   T tau, sigma;  // step scalars broadcast to every thread
   typename BatchSum<T>::type wacc, winv;
   unsigned long long t0;
-  long long cyc[5];  // SM cycles by phase (thread 0's clock between barriers)
+  long long cyc[8];  // SM cycles by phase (thread 0's clock between barriers)
   long long mark;    // thread 0's clock at the last phase boundary
   // normalized-gap evaluation (thread 0 keeps the bracket)
   int g_state, g_plan, ncand, first;
@@ -1229,7 +1232,7 @@ __device__ void solve_lp(const BatchLP<T>& L, const BatchParams& P, BatchResult*
     sh.tau = (T)(sh.eta / sh.omega);
     sh.sigma = (T)(sh.eta * sh.omega);
     sh.t0 = global_ns();
-    for (int q = 0; q < 5; ++q) sh.cyc[q] = 0;
+    for (int q = 0; q < 8; ++q) sh.cyc[q] = 0;
     sh.mark = clock64();
   }
 
@@ -1304,8 +1307,10 @@ __device__ void solve_lp(const BatchLP<T>& L, const BatchParams& P, BatchResult*
     const int c2 = sh.cur;
     const Pt<T> zc{L.X[c2], L.Y[c2], L.AX[c2], L.ATY[c2]};
     const Pt<T> za{L.Xa, L.Ya, L.AXa, L.ATYa};
+    batch_phase(sh, 3);
     const double mu_cur = cta_gap<T, NT>(L, zc, L.X0, L.Y0, sh.omega, sh, dsm);
     const double mu_avg = cta_gap<T, NT>(L, za, L.X0, L.Y0, sh.omega, sh, dsm);
+    batch_phase(sh, 5);
     if (threadIdx.x == 0) {
       // GetRestartCandidate: the average unless the current iterate's gap is smaller
       const bool avg = !(mu_cur < mu_avg);
@@ -1317,6 +1322,7 @@ __device__ void solve_lp(const BatchLP<T>& L, const BatchParams& P, BatchResult*
     const Pt<T> cand = cand_avg ? za : zc;
     if (is_check || is_limit) {
       cta_kkt<T, NT>(L, P, cand, sh);
+      batch_phase(sh, 6);
       if (threadIdx.x == 0) sh.dec_conv = converged(sh.kk, P) ? 1 : 0;
       __syncthreads();
       if (sh.dec_conv) {
@@ -1326,6 +1332,7 @@ __device__ void solve_lp(const BatchLP<T>& L, const BatchParams& P, BatchResult*
       }
       if (P.detect_infeasibility) {
         const int inf = cta_infeas<T, NT, B>(L, P, sh);
+        batch_phase(sh, 7);
         if (inf) {
           const int c = sh.flag;
           if (inf == PDLP_PRIMAL_INFEASIBLE) {
@@ -1398,7 +1405,9 @@ __device__ void solve_lp(const BatchLP<T>& L, const BatchParams& P, BatchResult*
       }
       __syncthreads();
       const double om = sh.im[1];
+      batch_phase(sh, 3);
       const double mu_ref = cta_gap<T, NT>(L, zc, L.X0, L.Y0, om, sh, dsm);
+      batch_phase(sh, 5);
       for (int64_t j = threadIdx.x; j < n; j += NT) {
         L.X0[j] = x[j];
         L.Sx[j] = 0;
@@ -1434,7 +1443,7 @@ __device__ void solve_lp(const BatchLP<T>& L, const BatchParams& P, BatchResult*
   batch_phase(sh, 4);
   if (threadIdx.x == 0) {
     BatchResult r;
-    for (int q = 0; q < 5; ++q) r.cycles[q] = sh.cyc[q];
+    for (int q = 0; q < 8; ++q) r.cycles[q] = sh.cyc[q];
     r.status = status;
     r.staged = (sx_on ? 1 : 0) | (sy_on ? 2 : 0);
     r.k = sh.k;
@@ -1493,7 +1502,7 @@ __global__ void __launch_bounds__(NT, PER_SM)
       for (int w = threadIdx.x; w < words; w += NT) dstw[w] = srcw[w];
     }
     __syncthreads();
-    solve_lp<T, NT, (NT * PER_SM >= 768 ? PDLP_BATCH_B_SMALL_REGS : 8)>(lp, prm, res + idx, sh, dsm, stage_bytes);
+    solve_lp<T, NT, (NT * PER_SM >= PDLP_BATCH_B_THRESHOLD ? PDLP_BATCH_B_SMALL_REGS : 8)>(lp, prm, res + idx, sh, dsm, stage_bytes);
   }
 }
 

@@ -1890,12 +1890,16 @@ static int batch_persistent(int64_t count, const pdlp_problem* problems, const p
                         6.0 * (double)n * v + 6.0 * (double)m * v;
     // device time by phase (the LP's time split by its SM cycles per phase)
     double cyc = 0.0;
-    for (int q = 0; q < 5; ++q) cyc += (double)r.cycles[q];
+    for (int q = 0; q < 8; ++q) cyc += (double)r.cycles[q];
     const double per = cyc > 0.0 ? 1e3 * r.seconds / cyc : 0.0;
     st->ms_primal = per * (double)r.cycles[0];
     st->ms_spmv_a = per * (double)r.cycles[1];
     st->ms_spmv_at = per * (double)r.cycles[2];
-    st->ms_checks = per * (double)(r.cycles[3] + r.cycles[4]);
+    st->ms_checks = per * (double)(r.cycles[3] + r.cycles[4] + r.cycles[5] + r.cycles[6] +
+                                   r.cycles[7]);
+    st->ms_gap = per * (double)r.cycles[5];
+    st->ms_kkt = per * (double)r.cycles[6];
+    st->ms_infeas = per * (double)r.cycles[7];
     st->batch_launch_s = launch_s;
     st->batch_sm = r.sm;
   }
