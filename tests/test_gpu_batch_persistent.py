@@ -165,3 +165,24 @@ def test_time_limit_and_rejected_arguments(pkg):
         _solve(pkg, [lpgen.config0()], feasibility_polishing=1)
     with pytest.raises(PdlpError):
         _solve(pkg, [lpgen.config0()], tune=7)
+
+
+def test_box_only_lp_and_empty_batch(pkg):
+    """An LP without rows (A is 0 x n) has the closed-form solution x_j = lv_j for
+    c_j > 0, uv_j for c_j < 0 (Sec. 2's box constraints alone); it solves in a batch with a
+    regular LP.  An empty batch returns at once."""
+    from tests import lp_helpers as H
+
+    rng = np.random.default_rng(3)
+    n = 700
+    c = rng.uniform(-1.0, 1.0, n)
+    lv, uv = rng.uniform(-5.0, 0.0, n), rng.uniform(0.0, 5.0, n)
+    box = H.make_lp(np.zeros((0, n)), c, [], [], lv, uv, name="box-only")
+    for prec in (0, 1):
+        got = _solve(pkg, [box, lpgen.config0()], precision=prec, eps_rel_kkt=1e-8)
+        assert got[0].status == 0 and got[1].status == 0
+        want = np.where(c > 0, lv, uv)
+        # FP32 bulk holds the scaled bounds in FP32: the returned x is within their rounding
+        assert np.allclose(got[0].x, want, rtol=0, atol=(1e-9 if prec == 0 else 1e-6) * 5.0)
+        assert got[0].y.size == 0
+    assert _solve(pkg, []) == []

@@ -148,3 +148,25 @@ def test_an_lp_too_large_fails_alone(pkg):
     assert got[0][0] == 0
     assert got[1][0] == -1
     assert "too large" in pkg.binding.load_library().pdlp_last_error().decode()
+
+
+def test_box_only_lp_and_empty_batch(pkg):
+    """An LP without rows: K steps of Eq. (3a) alone, x_K = proj_X(x - K tau c) reached
+    step by step, and the gradient of x_K wrt c is -tau K on the columns that never hit a
+    bound (each step moves x by -tau c); the single call gives the same."""
+    from tests import lp_helpers as H
+
+    rng = np.random.default_rng(4)
+    n = 300
+    c = rng.uniform(-1.0, 1.0, n)
+    lv, uv = np.full(n, -1e3), np.full(n, 1e3)
+    box = H.make_lp(np.zeros((0, n)), c, [], [], lv, uv, name="box-only")
+    it = dict(lp=box, K=40, eta=0.05, omega=1.0, gx=np.ones(n), gy=np.zeros(0), checkpoint_every=7)
+    (st, x, y, g), = pkg.binding.unrolled_pdhg_batch([it], persistent=True)
+    assert st == 0
+    tau = 0.05
+    assert np.allclose(x, -it["K"] * tau * c, rtol=1e-12, atol=1e-12)
+    assert np.allclose(g["c"], -it["K"] * tau, rtol=1e-12)
+    one = _single(pkg, it)
+    assert np.array_equal(x, one[0]) and np.array_equal(g["c"], one[2]["c"])
+    assert pkg.binding.unrolled_pdhg_batch([], persistent=True) == []
