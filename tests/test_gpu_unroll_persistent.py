@@ -170,3 +170,93 @@ def test_box_only_lp_and_empty_batch(pkg):
     one = _single(pkg, it)
     assert np.array_equal(x, one[0]) and np.array_equal(g["c"], one[2]["c"])
     assert pkg.binding.unrolled_pdhg_batch([], persistent=True) == []
+
+
+FD_H = 1e-6
+
+
+def _fd_instance(k):
+    """Instance k of the 16 central-difference LPs (the differentiable-batch shape), one
+    objective coordinate j and one equality row i to perturb, and the loss target."""
+    rng = np.random.default_rng(lpgen.config_seed(3) + 100 + k)
+    inst = lpgen.random_lp(2000, 5000, 8, seed=lpgen.config_seed(3, 100 + k))
+    A = inst.scipy_csr()
+    eta = 0.9 / np.sqrt(float(abs(A).sum(axis=0).max()) * float(abs(A).sum(axis=1).max()))
+    j = int(rng.integers(0, inst.n))
+    i = int(rng.choice(np.flatnonzero(inst.lc == inst.uc)))
+    return inst, eta, j, i, rng.uniform(0.0, 10.0, inst.n)
+
+
+def _moved(inst, kind, idx, step):
+    import dataclasses
+
+    if kind == "c":
+        c = inst.c.copy()
+        c[idx] += step
+        return dataclasses.replace(inst, c=c)
+    lc, uc = inst.lc.copy(), inst.uc.copy()  # an equality row: b_i moves both sides
+    lc[idx] += step
+    uc[idx] += step
+    return dataclasses.replace(inst, lc=lc, uc=uc)
+
+
+def test_differentiable_batch_central_differences_on_16_instances(pkg):
+    """Sixteen LPs of the differentiable-batch shape (2000 x 5000, 8 entries per column,
+    K = 2000, checkpoints every 50), loss ||x_K - x_target||^2: the adjoint's derivative
+    along one objective coordinate c_j and along one equality row's b_i (lc_i = uc_i
+    moved together) against the central difference (L(h) - L(-h)) / 2h with h = 1e-6,
+    every forward pass run by the same persistent launch in FP64.
+
+    x_K is piecewise affine in (c, b): the clamps of Eq. (3) switch where an iterate
+    meets a bound.  The central difference equals the derivative on one affine piece;
+    x_K(h) - x_K(0) against x_K(0) - x_K(-h) measures how far [-h, h] strays from one
+    piece (over 5000 x 2000 clamp decisions a few flip), and an instance whose second
+    difference r exceeds 1e-3 of the first is not a nondegenerate one and is left out
+    (at most 4 of 16).  The kinks inside [-h, h] move the central difference by about r
+    relative, the rounding of the 2000 steps by ~1e-5 absolute (1e-13 per entry of
+    x+ - x-, over 5000 entries, divided by 2h): the bound is 20 r |an| + 1e-4 max(1, |an|).
+    Measured in FP64 on the CPU for these 16: r up to 1.5e-3 along c_j (two instances
+    above 1e-3), under 1e-6 along b_i but one at 6e-5; |fd - an| at most 6.2 r |an| where r
+    exceeds 1e-5, otherwise at most 3.4e-5 relative and 2.5e-6 absolute.  The loss
+    difference is formed as (x+ - x-)'(x+ + x- - 2 x_target), equal to L(h) - L(-h)
+    without its cancellation.  The FP32-forward adjoint is held to the same differences at
+    1e-2 (relative l2 over the instances used)."""
+    cases = [_fd_instance(k) for k in range(16)]
+    fwd = []
+    for inst, eta, j, i, _ in cases:
+        fwd.append(dict(lp=inst, K=2000, eta=eta, omega=1.0))
+        for kind, idx in (("c", j), ("b", i)):
+            for s in (1.0, -1.0):
+                fwd.append(dict(lp=_moved(inst, kind, idx, s * FD_H), K=2000, eta=eta, omega=1.0))
+    got = pkg.binding.unrolled_pdhg_batch(fwd, persistent=True)
+    assert all(st == 0 for st, *_ in got)
+    xs = [x for _, x, _, _ in got]
+    grad_items = []
+    for k, (inst, eta, j, i, t) in enumerate(cases):
+        grad_items.append(dict(lp=inst, K=2000, eta=eta, omega=1.0, gx=2.0 * (xs[5 * k] - t),
+                               gy=np.zeros(inst.m), checkpoint_every=50))
+    g64 = pkg.binding.unrolled_pdhg_batch(grad_items, persistent=True)
+    g32 = pkg.binding.unrolled_pdhg_batch(grad_items, persistent=True, precision=pkg.FP32_BULK)
+    used = {"c": 0, "b": 0}
+    fd_all, an32_all = [], []
+    for k, (inst, eta, j, i, t) in enumerate(cases):
+        assert g64[k][0] == 0 and g32[k][0] == 0
+        x0 = xs[5 * k]
+        for d, (kind, idx) in enumerate((("c", j), ("b", i))):
+            xp, xm = xs[5 * k + 1 + 2 * d], xs[5 * k + 2 + 2 * d]
+            dp, dm = xp - x0, x0 - xm
+            r = float(np.linalg.norm(dp - dm)) / float(np.linalg.norm(dp))
+            if r > 1e-3:
+                continue
+            used[kind] += 1
+            fd = float((xp - xm) @ (xp + xm - 2.0 * t)) / (2.0 * FD_H)
+            g, gf = g64[k][3], g32[k][3]
+            an = g["c"][idx] if kind == "c" else g["lc"][idx] + g["uc"][idx]
+            an32 = gf["c"][idx] if kind == "c" else gf["lc"][idx] + gf["uc"][idx]
+            bound = 20.0 * r * abs(an) + 1e-4 * max(1.0, abs(an))
+            assert abs(fd - an) <= bound, (k, kind, fd, an, r)
+            fd_all.append(fd)
+            an32_all.append(an32)
+    assert used["c"] >= 12 and used["b"] >= 12, used
+    fd_all, an32_all = np.array(fd_all), np.array(an32_all)
+    assert np.linalg.norm(an32_all - fd_all) <= 1e-2 * np.linalg.norm(fd_all)
