@@ -479,6 +479,69 @@ static void build_problem(DeviceArena& arena, const Inputs& in, const DevInputs&
   }
 }
 
+// The FP32 copy of an FP64 layout: the same row order, long-row prefix and SELL slices
+// (index arrays shared with M), values rounded to FP32, and long-row scratch of its own.
+// Every FP32 value build_problem<float> stores is the rounding of the FP64 value that
+// build_problem<double> stores, so the copy equals the FP32 build of the same LP.
+static Mat<float> narrow_layout(DeviceArena& a, const Mat<double>& M, cudaStream_t s) {
+  Mat<float> F;
+  F.rows = M.rows;
+  F.cols = M.cols;
+  F.nnz = M.nnz;
+  F.row_ptr = M.row_ptr;
+  F.col = M.col;
+  F.R0 = M.R0;
+  F.nchunks = M.nchunks;
+  F.chunk_ptr = M.chunk_ptr;
+  F.chunk_owner = M.chunk_owner;
+  F.nslices = M.nslices;
+  F.slice_ptr = M.slice_ptr;
+  F.slice_len = M.slice_len;
+  F.sell_col = M.sell_col;
+  F.sell_entries = M.sell_entries;
+  int64_t ne = 0;  // entries of the long rows [0, R0)
+  if (M.R0) {
+    PDLP_CUDA_CHECK(cudaMemcpyAsync(&ne, M.row_ptr + M.R0, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+  }
+  F.val = a.alloc<float>(ne);
+  convert_values<float>(M.val, F.val, ne, s);
+  F.sell_val = a.alloc<float>(M.sell_entries);
+  convert_values<float>(M.sell_val, F.sell_val, M.sell_entries, s);
+  const int64_t R0 = M.R0;
+  F.long_cnt = a.alloc<unsigned int>(R0);
+  F.long_part = a.alloc<double>(M.nchunks);
+  F.long_contrib = a.alloc<double>(2 * R0);
+  F.sched = a.alloc<unsigned int>(2);
+  PDLP_CUDA_CHECK(cudaMemsetAsync(F.long_cnt, 0, sizeof(unsigned int) * std::max<int64_t>(1, R0), s));
+  PDLP_CUDA_CHECK(cudaMemsetAsync(F.long_contrib, 0, sizeof(double) * 2 * std::max<int64_t>(1, R0), s));
+  PDLP_CUDA_CHECK(cudaMemsetAsync(F.sched, 0, 2 * sizeof(unsigned int), s));
+  return F;
+}
+
+// The FP32 forward problem of the unrolled iteration from its FP64 build (identity
+// scaling): both layouts and the five vectors narrowed, the permutations shared.
+static void narrow_problem(DeviceArena& a, const Problem<double>& P, Problem<float>& F,
+                           cudaStream_t s) {
+  F.m = P.m;
+  F.n = P.n;
+  F.nnz = P.nnz;
+  F.A = narrow_layout(a, P.A, s);
+  F.AT = narrow_layout(a, P.AT, s);
+  F.perm_r = P.perm_r;
+  F.perm_c = P.perm_c;
+  auto vec = [&](const double* v, int64_t len) {
+    float* out = a.alloc<float>(len);
+    convert_values<float>(v, out, len, s);
+    return out;
+  };
+  F.c = vec(P.c, P.n);
+  F.lv = vec(P.lv, P.n);
+  F.uv = vec(P.uv, P.n);
+  F.lc = vec(P.lc, P.m);
+  F.uc = vec(P.uc, P.m);
+}
+
 // ---------------------------------------------------------------------------
 // the solver
 // ---------------------------------------------------------------------------
@@ -1981,7 +2044,7 @@ static void unroll_setup_one(UnrollItem<T>& it, const pdlp_unrolled_problem& u,
     L.uv = it.P.uv;
   } else {
     // FP32 forward: the same renumbered LP with FP32 values and vectors
-    build_problem<float>(a, in, d, 0, 0.0, it.P32, s);
+    narrow_problem(a, it.P, it.P32, s);
     L.A = it.P32.A;
     L.AT = it.P32.AT;
     L.c = it.P32.c;
@@ -2324,7 +2387,7 @@ int pdlp_unrolled_pdhg(int64_t m, int64_t n, const pdlp_csr* A, const double* c,
       // FP32 forward: the same renumbered LP with FP32 values and vectors (identity
       // scaling leaves the staged values as given); the reverse pass stays FP64
       Problem<float> P32;
-      build_problem<float>(arena, in, d, 0, 0.0, P32, s);
+      narrow_problem(arena, P, P32, s);
       const UnrolledFwd<float> F{P32.A, P32.AT, P32.c, P32.lc, P32.uc, P32.lv, P32.uv,
                                  (float)(eta / omega), (float)(eta * omega),
                                  spmv_grid<float>(P32.A, kEpiPlain), spmv_grid<float>(P32.AT, kEpiPlain)};
