@@ -380,7 +380,9 @@ int pdlp_unrolled_pdhg_batch(int64_t count, const pdlp_unrolled_problem* problem
  * 2 (m + n) forward values (FP64, or FP32 for PDLP_FP32_BULK) plus 8 (m + n) bytes within
  * 200 KB (about m + n <= 8500 in FP64, 12800 with an FP32 forward); a larger LP fails
  * alone with PDLP_INVALID_ARGUMENT.  params: precision, inputs_on_device and
- * cuda_stream as pdlp_unrolled_pdhg; the rest is ignored.  status_out[count] receives
+ * cuda_stream as pdlp_unrolled_pdhg; verbose = 1 prints one line to stderr with the host
+ * time of the call's phases (the setup, also by step summed over the LPs; the launch with
+ * the copies; the release); the rest is ignored.  status_out[count] receives
  * each LP's return value.  Returns 0 when every LP was attempted (pdlp_last_error()
  * then describes the first failed one), or PDLP_INVALID_ARGUMENT. */
 int pdlp_unrolled_pdhg_batch_persistent(int64_t count, const pdlp_unrolled_problem* problems,

@@ -1999,6 +1999,8 @@ struct UnrollItem {
   int64_t out_len[7] = {0, 0, 0, 0, 0, 0, 0};
   int code = 0;
   std::string err;
+  double setup_s[4] = {0.0, 0.0, 0.0, 0.0};  // host time: staging and validation, layouts,
+                                             // FP32 copy, buffers and the closing sync
 };
 
 template <class T>
@@ -2018,9 +2020,14 @@ static void unroll_setup_one(UnrollItem<T>& it, const pdlp_unrolled_problem& u,
                         " bytes); use pdlp_unrolled_pdhg_batch");
   DeviceArena& a = it.arena;
   const int64_t m = u.m, n = u.n;
+  auto t0 = Clock::now();
   DevInputs d = stage_inputs(a, in, s);
   validate(a, in, d, s);
+  it.setup_s[0] = secs_since(t0);
+  t0 = Clock::now();
   build_problem<double>(a, in, d, 0, 0.0, it.P, s);  // identity scaling, renumbered
+  it.setup_s[1] = secs_since(t0);
+  t0 = Clock::now();
   UnrollLP<T>& L = it.d;
   L.m = m;
   L.n = n;
@@ -2053,6 +2060,8 @@ static void unroll_setup_one(UnrollItem<T>& it, const pdlp_unrolled_problem& u,
     L.lv = it.P32.lv;
     L.uv = it.P32.uv;
   }
+  it.setup_s[2] = secs_since(t0);
+  t0 = Clock::now();
   const int64_t state = 2 * (m + n);
   L.cp = a.alloc<T>((L.K / L.C + 1) * state);
   L.seg = a.alloc<T>((L.C + 1) * state);
@@ -2091,6 +2100,7 @@ static void unroll_setup_one(UnrollItem<T>& it, const pdlp_unrolled_problem& u,
     for (int q = 0; q < 5; ++q) L.g[q] = a.alloc<double>(glen[q]);
   }
   PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+  it.setup_s[3] = secs_since(t0);
 }
 
 template <class T>
@@ -2102,6 +2112,7 @@ static int unroll_batch_persistent(int64_t count, const pdlp_unrolled_problem* p
   cudaStream_t s = sg.s;
   std::vector<std::unique_ptr<UnrollItem<T>>> items(count);
   for (auto& p : items) p.reset(new UnrollItem<T>());
+  const auto t_setup = Clock::now();
   {
     // the setup of one small LP is a chain of short launches and a few host
     // synchronisations, so many LPs are set up at once (48 workers instead of 16 changed
@@ -2140,6 +2151,8 @@ static int unroll_batch_persistent(int64_t count, const pdlp_unrolled_problem* p
     work();
     for (auto& t : pool) t.join();
   }
+  const double setup_s = secs_since(t_setup);
+  const auto t_run = Clock::now();
   std::vector<int32_t> order;
   for (int64_t i = 0; i < count; ++i)
     if (items[i]->code == 0) order.push_back((int32_t)i);
@@ -2173,6 +2186,7 @@ static int unroll_batch_persistent(int64_t count, const pdlp_unrolled_problem* p
     }
     PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
   }
+  const double run_s = secs_since(t_run);
   std::string first_error;
   for (int64_t i = 0; i < count; ++i) {
     status_out[i] = items[i]->code;
@@ -2180,6 +2194,21 @@ static int unroll_batch_persistent(int64_t count, const pdlp_unrolled_problem* p
       first_error = "problem " + std::to_string(i) + ": " + items[i]->err;
   }
   if (!first_error.empty()) set_last_error(first_error);
+  if (prm.verbose) {
+    double per[4] = {0.0, 0.0, 0.0, 0.0};  // summed over the LPs (the workers overlap)
+    for (const auto& it : items)
+      for (int q = 0; q < 4; ++q) per[q] += it->setup_s[q];
+    const auto t_rel = Clock::now();
+    arena.release();
+    items.clear();
+    PDLP_CUDA_CHECK(cudaStreamSynchronize(s));
+    std::fprintf(stderr,
+                 "pdlp: unrolled batch of %lld LPs: setup %.3f s (summed over LPs: staging %.3f, "
+                 "layouts %.3f, FP32 copy %.3f, buffers %.3f), launch and copies %.3f s, "
+                 "release %.3f s\n",
+                 (long long)count, setup_s, per[0], per[1], per[2], per[3], run_s,
+                 secs_since(t_rel));
+  }
   return 0;
 }
 
